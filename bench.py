@@ -1,0 +1,330 @@
+"""Benchmark of the GPP self-energy summation on GB300.
+
+Workload: the paper-shaped benchmark instance (number_bands=512, ngpown=1638, ncouls=32768,
+nw=3; synthetic seeded inputs standing in for BerkeleyGW's Si-214/Si-510). One step is one
+``gpp_sigma`` FP64 call (column gather, main sum, final reduction) on inputs resident in
+HBM. The metric is FP64 TFLOP/s from the fixed model FLOP count (159 per band x igp x ig at
+nw=3), with the fraction of the FP64 peak measured in the same run by DFMA-chain kernels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpp|reference]
+
+Prints one JSON line on rank 0. ``--impl reference`` times the CPU oracle (the plain FP64
+reference implementation) on a band sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GPP FP64 TFLOP/s & %peak at 512x1638x32768x3; FP32-bulk speedup at <=1e-6 err"
+UNIT = "TFLOP/s"
+WORKLOAD = "gpp_benchmark_B512_P1638_G32768_nw3"
+ORACLE_SAMPLE_BANDS = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpp", "reference"], default="gpp")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def base_config(args, world):
+    from paper_2008_11326_gb300 import inputs
+    c = inputs.CONFIGS["benchmark"]
+    return {"workload": WORKLOAD, "number_bands": c["number_bands"], "ngpown": c["ngpown"],
+            "ncouls": c["ncouls"], "nw": c["nw"], "nvband": c["nvband"], "occ_mode": "all",
+            "seed": c["seed"], "parallelism": f"replicas{world}" if world > 1 else "single",
+            "l2": "inputs (2.0 GB) larger than L2 (129 MB); no flush needed"}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(prob, bands: int, nthreads: int):
+    """Time the CPU oracle, as it stands, on the first ``bands`` bands of the instance."""
+    import oracle
+    from paper_2008_11326_gb300 import inputs
+    sub = prob.bands(slice(0, bands))
+    t0 = time.perf_counter()
+    oracle.sigma(sub, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    flops = inputs.model_flops(sub.number_bands, sub.ngpown, sub.ncouls, sub.nw)
+    return flops / dt / 1e12, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2008_11326_gb300 import inputs
+    oracle.build()
+    prob = inputs.config("benchmark")
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(prob, 1, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample(prob, ORACLE_SAMPLE_BANDS, cores)
+        times.append(dt)
+    flops = inputs.model_flops(ORACLE_SAMPLE_BANDS, prob.ngpown, prob.ncouls, prob.nw)
+    t = statistics.mean(times)
+    value = flops / t / 1e12
+    sample = (f"first {ORACLE_SAMPLE_BANDS} of 512 bands of the benchmark instance per step "
+              f"({flops:.3e} model FLOP), OpenMP over igp")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": base_config(args, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        pw = [num(r[3]) for r in rows if num(r[3])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows),
+                "reasons": reasons}
+
+
+def measure_peaks(torch, gpp, device):
+    """FP64 (DFMA) and FP32 (FFMA) peaks from the library's throughput kernels."""
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float64, device=device)
+    out = {}
+    for kind, iters, bps in (("dfma", 256, 4), ("ffma", 8192, 8), ("drcp", 128, 4)):
+        blocks, threads = sms * bps, 256
+        gpp.peak_launch(kind, iters // 8, blocks, threads, sink)  # warm
+        torch.cuda.synchronize(device)
+        best = 0.0
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = gpp.peak_launch(kind, iters, blocks, threads, sink)
+            e1.record()
+            e1.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) * 1e-3))
+        out[kind] = best
+    return {"fp64_tflops": 2 * out["dfma"] / 1e12, "fp32_tflops": 2 * out["ffma"] / 1e12,
+            "fp64_rcp_per_s": out["drcp"], "sms": sms}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2008_11326_gb300 import gpp, inputs
+
+    rank, world, local = dist_env()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    prob = inputs.config("benchmark")
+    dp = gpp.DeviceProblem.from_host(prob, device=device)
+    flops = inputs.model_flops(prob.number_bands, prob.ngpown, prob.ncouls, prob.nw)
+    h2d_bytes = prob.nbytes()
+    ws = torch.empty(gpp.workspace_size(dp), dtype=torch.uint8, device=device)
+    ach = torch.empty(prob.nw, dtype=torch.complex128, device=device)
+    asx = torch.empty(prob.nw, dtype=torch.complex128, device=device)
+
+    peaks = measure_peaks(torch, gpp, device)
+
+    K, W = args.steps, args.warmup
+    stage = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for evs in stage:  # materialise the events so their handles exist
+        for e in evs:
+            e.record()
+    torch.cuda.synchronize(device)
+
+    for _ in range(W):
+        gpp.sigma(dp, out=(ach, asx), workspace=ws)
+    torch.cuda.synchronize(device)
+    ref_a = ach.cpu().numpy().copy()
+    ref_s = asx.cpu().numpy().copy()
+
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as clk:
+        t0.record()
+        for k in range(K):
+            gpp.sigma(dp, out=(ach, asx), workspace=ws, stage_events=stage[k])
+        t1.record()
+        torch.cuda.synchronize(device)
+    barrier()
+    total_ms = t0.elapsed_time(t1)
+    main_ms = [stage[k][1].elapsed_time(stage[k][2]) for k in range(K)]
+    step_ms = total_ms / K
+    if pg is not None:
+        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * flops / (step_ms * 1e-3) / 1e12
+    deterministic = bool(np.array_equal(ach.cpu().numpy(), ref_a) and
+                         np.array_equal(asx.cpu().numpy(), ref_s))
+
+    # end to end through the host-array entry point: H2D of every input, sum, D2H
+    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True)
+    del dp
+    torch.cuda.empty_cache()
+    hws = torch.empty(gpp.host_workspace_size(hp), dtype=torch.uint8, device=device)
+    hout = (torch.empty(prob.nw, dtype=torch.complex128).pin_memory(),
+            torch.empty(prob.nw, dtype=torch.complex128).pin_memory())
+    gpp.sigma_host(hp, workspace=hws, out=hout)
+    e2e_steps = max(1, args.e2e_steps)
+    torch.cuda.synchronize(device)
+    s0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gpp.sigma_host(hp, workspace=hws, out=hout)
+    e2e_s = (time.perf_counter() - s0) / e2e_steps
+    e2e_ok = bool(np.array_equal(hout[0].numpy(), ref_a) and np.array_equal(hout[1].numpy(), ref_s))
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    main_avg_s = statistics.mean(main_ms) * 1e-3
+    achieved = flops / main_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"], "traffic": None,
+                "kernel": "gpp_fwd_f64_kernel<3>",
+                "peak_source": "DFMA-chain throughput kernel measured in this run, all SMs "
+                               "(FP64 pipe; FMA = 2 FLOP)",
+                "achieved_source": "model FLOP (159 per band x igp x ig) / mean CUDA-event "
+                                   "duration of the main kernel over the timed steps"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, dt = oracle_sample(prob, ORACLE_SAMPLE_BANDS, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {ORACLE_SAMPLE_BANDS} of 512 bands of the benchmark instance "
+                         f"({dt:.1f} s, OpenMP over igp on all host cores)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": base_config(args, world),
+            "fp64_peak_frac": value / world / peaks["fp64_tflops"],
+            "main_kernel_ms": statistics.mean(main_ms),
+            "peaks_measured": peaks,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * flops / e2e_s / 1e12, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 2 * prob.nw * 16,
+                    "steps": e2e_steps, "matches_device_result": e2e_ok},
+            "gpu_launches": 3 * K,
+            "deterministic_across_steps": deterministic,
+            "clocks": clk.summary(),
+            "fp32_bulk": None}
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

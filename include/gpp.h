@@ -1,0 +1,169 @@
+/*
+ * libgpp: General Plasmon Pole (GPP) self-energy summation on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (paper §II-A, the loop nest over band, igp, ig and iw; §III v2, the
+ * three-way branch; §III v3, predicates on squared moduli). For every band b, local column
+ * p, G-vector ig and frequency iw:
+ *
+ *   g      = indinv[inv_igp_index[p]]  (global column; if inv_igp_index[p] is outside
+ *                                       [0, ncouls] or g is outside [0, ncouls), column p
+ *                                       contributes nothing -- indinv[ncouls] = ncouls is
+ *                                       the sentinel)
+ *   M      = conj(aqsmtemp[b][g]) * aqsntemp[b][ig] * vcoul[g]
+ *   x      = wx_array[b][iw],  w = wtilde_array[p][ig],  I = I_eps_array[p][ig]
+ *   wdiff  = x - w,  wdiffr = |wdiff|^2,  delw = w / wdiff,  delwr = |delw|^2
+ *   branch 1, wdiffr > 0.25 and delwr < 2.5e5:  sch = delw I,  ssx = w^2 I / (x^2 - w^2)
+ *   branch 2, else if delwr > 1e-12:           sch = 0,       ssx = -I delw / (4 delw + 2)
+ *   branch 3, else:                             sch = 0,       ssx = 0
+ *   achtemp[iw] = sum M sch,   asxtemp[iw] = sum occ(b) M ssx
+ *
+ * with occ(b) = 1 (GPP_OCC_ALL) or [b < nvband] (GPP_OCC_OCCUPIED). The paper names the
+ * three thresholds without printing them or the sch/ssx formulas; the values above are the
+ * generalised plasmon-pole terms of BerkeleyGW, which the paper's kernel is taken from.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are C row-major with the last index contiguous; complex arrays are interleaved
+ *    (re, im) pairs, the layout of torch complex128 / complex64. Shapes:
+ *      aqsmtemp, aqsntemp [number_bands][ncouls]; I_eps_array, wtilde_array
+ *      [ngpown][ncouls]; vcoul [ncouls]; inv_igp_index [ngpown]; indinv [ncouls + 1];
+ *      wx_array [number_bands][nw]; achtemp, asxtemp [nw].
+ *  - Data pointers are DEVICE pointers owned by the caller; inputs are only read, outputs
+ *    are fully overwritten. Complex arrays must be 16-byte aligned (c128) or 8-byte aligned
+ *    (c64). The caller provides the workspace; the library allocates no device memory.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *    default stream) unless stated otherwise.
+ *  - Results are bit-for-bit deterministic for fixed inputs, options and device.
+ *  - Return GPP_OK (0) or a negative gpp_status; gpp_last_error() then describes it.
+ */
+#ifndef GPP_H
+#define GPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GPP_API __attribute__((visibility("default")))
+#else
+#define GPP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gpp_status {
+    GPP_OK = 0,
+    GPP_ERR_NULL_PTR = -1,    /* a required pointer is NULL */
+    GPP_ERR_BAD_SIZE = -2,    /* a size is negative, nw outside [1, GPP_MAX_NW], or a size exceeds 32-bit indexing */
+    GPP_ERR_BAD_INDEX = -3,   /* debug_checks found an index outside its range */
+    GPP_ERR_WORKSPACE = -4,   /* workspace NULL, misaligned or smaller than required */
+    GPP_ERR_CUDA = -5,        /* a CUDA call or kernel launch failed */
+    GPP_ERR_UNSUPPORTED = -6, /* option combination not supported */
+    GPP_ERR_TIMEOUT = -7,     /* a bounded device-side wait gave up */
+    GPP_ERR_BAD_OPTION = -8   /* an option field has an unknown value */
+} gpp_status;
+
+typedef enum gpp_precision {
+    GPP_FP64 = 0,      /* every step in FP64 */
+    GPP_FP32_BULK = 1  /* FP32 complex arithmetic on complex64 copies, FP64 where it matters */
+} gpp_precision;
+
+typedef enum gpp_occ_mode {
+    GPP_OCC_ALL = 0,      /* occ(b) = 1: every band enters asxtemp (the paper's loop nest) */
+    GPP_OCC_OCCUPIED = 1  /* occ(b) = [b < nvband] */
+} gpp_occ_mode;
+
+#define GPP_MAX_NW 8
+
+typedef struct gpp_c128 {
+    double re, im;
+} gpp_c128;
+
+typedef struct gpp_c64 {
+    float re, im;
+} gpp_c64;
+
+/* One GPP instance. Names follow the paper's kernel. */
+typedef struct gpp_problem {
+    int64_t number_bands; /* B >= 0 */
+    int64_t nvband;       /* V >= 0, used by GPP_OCC_OCCUPIED */
+    int64_t ncouls;       /* G >= 0 */
+    int64_t ngpown;       /* P >= 0 */
+    int64_t nw;           /* W, 1 <= W <= GPP_MAX_NW */
+    const gpp_c128 *aqsmtemp;     /* [B][G] */
+    const gpp_c128 *aqsntemp;     /* [B][G] */
+    const gpp_c128 *I_eps_array;  /* [P][G] */
+    const gpp_c128 *wtilde_array; /* [P][G] */
+    const double *vcoul;          /* [G] */
+    const int32_t *inv_igp_index; /* [P] */
+    const int32_t *indinv;        /* [G + 1] */
+    const double *wx_array;       /* [B][W] */
+    /* complex64 copies, read by GPP_FP32_BULK (NULL otherwise) */
+    const gpp_c64 *aqsmtemp_c64;     /* [B][G] */
+    const gpp_c64 *aqsntemp_c64;     /* [B][G] */
+    const gpp_c64 *I_eps_array_c64;  /* [P][G] */
+    const gpp_c64 *wtilde_array_c64; /* [P][G] */
+    gpp_c128 *achtemp; /* [W] output */
+    gpp_c128 *asxtemp; /* [W] output */
+} gpp_problem;
+
+typedef struct gpp_options {
+    int32_t precision;     /* gpp_precision */
+    int32_t occ_mode;      /* gpp_occ_mode */
+    int32_t block_threads; /* threads per CTA of the main kernel: 0 = default (128), else a multiple of 32 in [64, 256] */
+    int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = default */
+    int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
+    int32_t reserved[3];   /* must be 0 */
+    /* NULL, or an array of 4 cudaEvent_t (passed as void*) that the call records on its
+     * stream: [0] before the column gather, [1] before the main sum, [2] after it, [3] after
+     * the final reduction. For timing the main kernel; the events belong to the caller. */
+    void *const *stage_events;
+} gpp_options;
+
+/* Fills *opt with the defaults (GPP_FP64, GPP_OCC_ALL, default tiles, no debug checks). */
+GPP_API void gpp_options_default(gpp_options *opt);
+
+/*
+ * Workspace bytes that gpp_sigma needs for this problem and these options on the current
+ * device (it depends on the SM count). 0 with gpp_last_error() set if the arguments are
+ * invalid. Pure host computation; no device memory is touched.
+ */
+GPP_API size_t gpp_sigma_workspace_size(const gpp_problem *prob, const gpp_options *opt);
+
+/*
+ * The forward sum (achtemp, asxtemp) of one instance. `workspace` is a device buffer of at
+ * least gpp_sigma_workspace_size() bytes, 256-byte aligned, owned by the caller and not
+ * used concurrently by another call. The call enqueues three kernels on `stream` (column
+ * gather, main sum, deterministic final reduction) and returns without synchronising,
+ * except with debug_checks = 1, where it synchronises `stream` to report bad indices.
+ * Errors: NULL_PTR, BAD_SIZE, BAD_OPTION, WORKSPACE, CUDA, BAD_INDEX (debug_checks only).
+ */
+GPP_API int gpp_sigma(const gpp_problem *prob, const gpp_options *opt, void *workspace,
+              size_t workspace_bytes, void *stream);
+
+/*
+ * Device bytes that gpp_sigma_host needs: room for device copies of every input array
+ * plus gpp_sigma's own workspace.
+ */
+GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_options *opt);
+
+/*
+ * gpp_sigma on HOST arrays: every pointer in `prob` (inputs and outputs) is a host pointer
+ * (page-locked memory gives the fastest copies). The inputs are copied into `workspace`
+ * (a device buffer of gpp_sigma_host_workspace_size() bytes), the sum runs, the outputs
+ * are copied back, and the call returns after `stream` has finished (it synchronises).
+ */
+GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void *workspace,
+                   size_t workspace_bytes, void *stream);
+
+/* Thread-local description of the last error on this host thread ("" if none). */
+GPP_API const char *gpp_last_error(void);
+
+/* Library version string. */
+GPP_API const char *gpp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPP_H */

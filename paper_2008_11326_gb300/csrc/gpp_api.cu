@@ -1,0 +1,341 @@
+// C-ABI entry points of libgpp (declared in include/gpp.h): argument validation,
+// workspace layout and kernel launches. No entry point allocates device memory.
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "gpp.h"
+#include "gpp_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GPP_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+gpp_options defaults() {
+  gpp_options o;
+  memset(&o, 0, sizeof(o));
+  o.precision = GPP_FP64;
+  o.occ_mode = GPP_OCC_ALL;
+  return o;
+}
+
+bool degenerate(const gpp_problem& p) {
+  return p.number_bands == 0 || p.ngpown == 0 || p.ncouls == 0;
+}
+
+int check_options(const gpp_options& o) {
+  if (o.precision != GPP_FP64 && o.precision != GPP_FP32_BULK)
+    return fail(GPP_ERR_BAD_OPTION, "precision %d is not GPP_FP64 or GPP_FP32_BULK", o.precision);
+  if (o.occ_mode != GPP_OCC_ALL && o.occ_mode != GPP_OCC_OCCUPIED)
+    return fail(GPP_ERR_BAD_OPTION, "occ_mode %d is not GPP_OCC_ALL or GPP_OCC_OCCUPIED", o.occ_mode);
+  if (o.block_threads != 0 &&
+      (o.block_threads < 64 || o.block_threads > 256 || o.block_threads % 32 != 0))
+    return fail(GPP_ERR_BAD_OPTION, "block_threads %d must be 0 or a multiple of 32 in [64, 256]",
+                o.block_threads);
+  if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64)
+    return fail(GPP_ERR_BAD_OPTION, "blocks_per_sm %d must be in [0, 64]", o.blocks_per_sm);
+  if (o.debug_checks != 0 && o.debug_checks != 1)
+    return fail(GPP_ERR_BAD_OPTION, "debug_checks must be 0 or 1");
+  for (int i = 0; i < 3; ++i)
+    if (o.reserved[i] != 0) return fail(GPP_ERR_BAD_OPTION, "reserved option fields must be 0");
+  return GPP_OK;
+}
+
+int check_sizes(const gpp_problem& p) {
+  if (p.number_bands < 0 || p.nvband < 0 || p.ncouls < 0 || p.ngpown < 0)
+    return fail(GPP_ERR_BAD_SIZE, "negative size (number_bands %lld nvband %lld ncouls %lld ngpown %lld)",
+                (long long)p.number_bands, (long long)p.nvband, (long long)p.ncouls,
+                (long long)p.ngpown);
+  if (p.nw < 1 || p.nw > GPP_MAX_NW)
+    return fail(GPP_ERR_BAD_SIZE, "nw %lld outside [1, %d]", (long long)p.nw, GPP_MAX_NW);
+  if (p.number_bands > INT32_MAX || p.ncouls >= INT32_MAX || p.ngpown > INT32_MAX)
+    return fail(GPP_ERR_BAD_SIZE, "sizes must fit 32-bit indices");
+  return GPP_OK;
+}
+
+// Pointers the forward pass reads for this precision; complex arrays 16- or 8-byte aligned.
+int check_pointers(const gpp_problem& p, int precision) {
+  if (!p.achtemp || !p.asxtemp) return fail(GPP_ERR_NULL_PTR, "achtemp and asxtemp must be non-NULL");
+  if (!aligned(p.achtemp, 16) || !aligned(p.asxtemp, 16))
+    return fail(GPP_ERR_NULL_PTR, "achtemp / asxtemp must be 16-byte aligned");
+  if (degenerate(p)) return GPP_OK;
+  struct {
+    const void* ptr;
+    const char* name;
+    size_t align;
+  } req[] = {{p.aqsmtemp, "aqsmtemp", 16},     {p.aqsntemp, "aqsntemp", 16},
+             {p.I_eps_array, "I_eps_array", 16}, {p.wtilde_array, "wtilde_array", 16},
+             {p.vcoul, "vcoul", 8},             {p.inv_igp_index, "inv_igp_index", 4},
+             {p.indinv, "indinv", 4},           {p.wx_array, "wx_array", 8}};
+  for (auto& r : req) {
+    if (!r.ptr) return fail(GPP_ERR_NULL_PTR, "%s is NULL", r.name);
+    if (!aligned(r.ptr, r.align)) return fail(GPP_ERR_NULL_PTR, "%s is not %zu-byte aligned", r.name, r.align);
+  }
+  if (precision == GPP_FP32_BULK) {
+    const void* c64[] = {p.aqsntemp_c64, p.I_eps_array_c64, p.wtilde_array_c64};
+    const char* names[] = {"aqsntemp_c64", "I_eps_array_c64", "wtilde_array_c64"};
+    for (int i = 0; i < 3; ++i) {
+      if (!c64[i]) return fail(GPP_ERR_NULL_PTR, "%s is NULL (GPP_FP32_BULK)", names[i]);
+      if (!aligned(c64[i], 8)) return fail(GPP_ERR_NULL_PTR, "%s is not 8-byte aligned", names[i]);
+    }
+  }
+  return GPP_OK;
+}
+
+int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan) {
+  gpp::FwdPlan pl;
+  pl.nw = static_cast<int>(p.nw);
+  pl.threads = o.block_threads ? o.block_threads : 128;
+  if (degenerate(p)) {
+    *plan = pl;
+    return GPP_OK;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+  int bps = o.blocks_per_sm;
+  if (bps == 0) {
+    bps = (o.precision == GPP_FP32_BULK) ? gpp::fwd_f32_blocks_per_sm(pl.threads, pl.nw)
+                                         : gpp::fwd_f64_blocks_per_sm(pl.threads, pl.nw);
+    if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for %d threads", pl.threads);
+  }
+  pl.n_ig_tiles = (p.ncouls + pl.threads - 1) / pl.threads;
+  pl.ntiles = p.ngpown * pl.n_ig_tiles;
+  int64_t grid = static_cast<int64_t>(sms) * bps;
+  if (grid > pl.ntiles) grid = pl.ntiles;
+  if (grid < 1) grid = 1;
+  pl.grid = static_cast<int>(grid);
+  size_t off = 0;
+  pl.off_flags = off;
+  off = gpp::align_up(off + 4 * sizeof(int));
+  pl.off_colvalid = off;
+  off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * sizeof(int));
+  pl.off_bt = off;
+  off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 4 * sizeof(double));
+  pl.off_am = off;
+  off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(double));
+  pl.off_partials = off;
+  off = gpp::align_up(off + static_cast<size_t>(pl.grid) * 4 * p.nw * sizeof(double));
+  pl.total = off;
+  *plan = pl;
+  return GPP_OK;
+}
+
+int validate(const gpp_problem* prob, const gpp_options* opt, gpp_options* o) {
+  if (!prob) return fail(GPP_ERR_NULL_PTR, "problem is NULL");
+  *o = opt ? *opt : defaults();
+  int rc = check_options(*o);
+  if (rc) return rc;
+  return check_sizes(*prob);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gpp_options_default(gpp_options* opt) {
+  if (opt) *opt = defaults();
+}
+
+const char* gpp_last_error(void) { return g_last_error.c_str(); }
+
+const char* gpp_version(void) { return "libgpp 0.1 (sm_103a)"; }
+
+size_t gpp_sigma_workspace_size(const gpp_problem* prob, const gpp_options* opt) {
+  gpp_options o;
+  if (validate(prob, opt, &o)) return 0;
+  gpp::FwdPlan plan;
+  if (make_plan(*prob, o, &plan)) return 0;
+  g_last_error.clear();
+  return plan.total;
+}
+
+int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
+              size_t workspace_bytes, void* stream) {
+  gpp_options o;
+  int rc = validate(prob, opt, &o);
+  if (rc) return rc;
+  const gpp_problem& p = *prob;
+  if ((rc = check_pointers(p, o.precision))) return rc;
+  if (o.precision == GPP_FP32_BULK && !gpp::fwd_f32_available())
+    return fail(GPP_ERR_UNSUPPORTED, "GPP_FP32_BULK is not built into this library");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (degenerate(p)) {
+    cudaError_t e = cudaMemsetAsync(p.achtemp, 0, p.nw * sizeof(gpp_c128), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.asxtemp, 0, p.nw * sizeof(gpp_c128), s);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing the outputs");
+    g_last_error.clear();
+    return GPP_OK;
+  }
+  gpp::FwdPlan plan;
+  if ((rc = make_plan(p, o, &plan))) return rc;
+  if (!workspace) return fail(GPP_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", plan.total);
+  if (!aligned(workspace, gpp::kAlign)) return fail(GPP_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (workspace_bytes < plan.total)
+    return fail(GPP_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", workspace_bytes, plan.total);
+  char* ws = static_cast<char*>(workspace);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (o.stage_events)
+    for (int i = 0; i < 4; ++i) ev[i] = static_cast<cudaEvent_t>(o.stage_events[i]);
+  auto mark = [&](int i) -> cudaError_t { return ev[i] ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+  cudaError_t e = mark(0);
+  if (e != cudaSuccess) return cuda_fail(e, "recording stage event 0");
+  e = gpp::launch_prep(p, plan, ws, o.precision == GPP_FP32_BULK, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  if (o.debug_checks) {
+    int flags[4];
+    e = cudaMemcpyAsync(flags, ws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
+    if (flags[1] > 0)
+      return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
+                  flags[1]);
+  }
+  if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "recording stage event 1");
+  if (o.precision == GPP_FP64)
+    e = gpp::launch_fwd_f64(p, o.occ_mode, plan, ws, s);
+  else
+    e = gpp::launch_fwd_f32(p, o.occ_mode, plan, ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the main sum");
+  if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "recording stage event 2");
+  e = gpp::launch_reduce_final(plan, ws, p.achtemp, p.asxtemp, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the final reduction");
+  if ((e = mark(3)) != cudaSuccess) return cuda_fail(e, "recording stage event 3");
+  if (o.debug_checks) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "running the sum");
+  }
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host-array variant: copies in, runs gpp_sigma on device copies inside the workspace,
+// copies the outputs back and synchronises.
+
+namespace {
+
+struct HostLayout {
+  size_t off[12];
+  size_t sigma_off;
+  size_t total;
+};
+
+// Segment order: aqsm, aqsn, eps, wt, vcoul, inv, indinv, wx, aqsn_c64, eps_c64, wt_c64,
+// outputs (ach then asx).
+void host_layout(const gpp_problem& p, int precision, size_t sigma_bytes, HostLayout* L) {
+  const size_t B = p.number_bands, G = p.ncouls, P = p.ngpown, W = p.nw;
+  const bool f32 = precision == GPP_FP32_BULK;
+  size_t sizes[12] = {B * G * 16, B * G * 16, P * G * 16, P * G * 16, G * 8, P * 4, (G + 1) * 4,
+                      B * W * 8,  f32 ? B * G * 8 : 0, f32 ? P * G * 8 : 0, f32 ? P * G * 8 : 0,
+                      2 * W * 16};
+  size_t off = 0;
+  for (int i = 0; i < 12; ++i) {
+    L->off[i] = off;
+    off = gpp::align_up(off + sizes[i]);
+  }
+  L->sigma_off = off;
+  L->total = gpp::align_up(off + sigma_bytes);
+}
+
+}  // namespace
+
+size_t gpp_sigma_host_workspace_size(const gpp_problem* prob, const gpp_options* opt) {
+  gpp_options o;
+  if (validate(prob, opt, &o)) return 0;
+  gpp::FwdPlan plan;
+  if (make_plan(*prob, o, &plan)) return 0;
+  HostLayout L;
+  host_layout(*prob, o.precision, plan.total, &L);
+  g_last_error.clear();
+  return L.total;
+}
+
+int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* workspace,
+                   size_t workspace_bytes, void* stream) {
+  gpp_options o;
+  int rc = validate(prob, opt, &o);
+  if (rc) return rc;
+  const gpp_problem& h = *prob;
+  if ((rc = check_pointers(h, o.precision))) return rc;
+  gpp::FwdPlan plan;
+  if ((rc = make_plan(h, o, &plan))) return rc;
+  HostLayout L;
+  host_layout(h, o.precision, plan.total, &L);
+  if (!workspace || !aligned(workspace, gpp::kAlign) || workspace_bytes < L.total)
+    return fail(GPP_ERR_WORKSPACE, "host-call workspace must be 256-byte aligned with %zu bytes",
+                L.total);
+  char* ws = static_cast<char*>(workspace);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t B = h.number_bands, G = h.ncouls, P = h.ngpown, W = h.nw;
+  const bool f32 = o.precision == GPP_FP32_BULK;
+  struct {
+    const void* src;
+    size_t bytes;
+    int seg;
+  } copies[] = {{h.aqsmtemp, B * G * 16, 0},
+                {h.aqsntemp, B * G * 16, 1},
+                {h.I_eps_array, P * G * 16, 2},
+                {h.wtilde_array, P * G * 16, 3},
+                {h.vcoul, G * 8, 4},
+                {h.inv_igp_index, P * 4, 5},
+                {h.indinv, (G + 1) * 4, 6},
+                {h.wx_array, B * W * 8, 7},
+                {f32 ? h.aqsntemp_c64 : nullptr, B * G * 8, 8},
+                {f32 ? h.I_eps_array_c64 : nullptr, P * G * 8, 9},
+                {f32 ? h.wtilde_array_c64 : nullptr, P * G * 8, 10}};
+  gpp_problem d = h;
+  void* dptr[11];
+  for (int i = 0; i < 11; ++i) {
+    dptr[i] = ws + L.off[copies[i].seg];
+    if (!copies[i].src || copies[i].bytes == 0) continue;
+    cudaError_t e = cudaMemcpyAsync(dptr[i], copies[i].src, copies[i].bytes,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copying inputs to the device");
+  }
+  d.aqsmtemp = static_cast<const gpp_c128*>(dptr[0]);
+  d.aqsntemp = static_cast<const gpp_c128*>(dptr[1]);
+  d.I_eps_array = static_cast<const gpp_c128*>(dptr[2]);
+  d.wtilde_array = static_cast<const gpp_c128*>(dptr[3]);
+  d.vcoul = static_cast<const double*>(dptr[4]);
+  d.inv_igp_index = static_cast<const int32_t*>(dptr[5]);
+  d.indinv = static_cast<const int32_t*>(dptr[6]);
+  d.wx_array = static_cast<const double*>(dptr[7]);
+  d.aqsmtemp_c64 = nullptr;
+  d.aqsntemp_c64 = f32 ? static_cast<const gpp_c64*>(dptr[8]) : nullptr;
+  d.I_eps_array_c64 = f32 ? static_cast<const gpp_c64*>(dptr[9]) : nullptr;
+  d.wtilde_array_c64 = f32 ? static_cast<const gpp_c64*>(dptr[10]) : nullptr;
+  d.achtemp = reinterpret_cast<gpp_c128*>(ws + L.off[11]);
+  d.asxtemp = d.achtemp + W;
+  rc = gpp_sigma(&d, &o, ws + L.sigma_off, L.total - L.sigma_off, stream);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(h.achtemp, d.achtemp, W * 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.asxtemp, d.asxtemp, W * 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "copying the outputs back");
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+}  // extern "C"

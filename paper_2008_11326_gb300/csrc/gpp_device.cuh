@@ -1,0 +1,88 @@
+// Device-side building blocks shared by the GPP kernels: constants of the plasmon-pole
+// branch, the FP64 reciprocal, bit-pattern comparisons and the deterministic reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpp {
+
+// Thresholds of the three-way branch (paper §III v2), compared against squared moduli
+// (§III v3): |wdiff|^2 > LIMITTWO and |delw|^2 < LIMITONE select branch 1, otherwise
+// |delw|^2 > TOL_ZERO selects branch 2.
+constexpr double kLimitTwo = 0.25;
+constexpr double kLimitOne = 250000.0;  // 1 / (4 * 1e-6)
+constexpr double kTolZero = 1.0e-12;
+constexpr long long kLimitTwoBits = 0x3FD0000000000000LL;  // bit pattern of 0.25
+
+// The fast path decides branch 1 from |wdiff|^2 alone. That is exact when
+// 1e-12 < |w|^2 < 62499: then |wdiff|^2 > 1/4 implies |delw|^2 = |w|^2/|wdiff|^2 < 249996
+// (below LIMITONE by far more than rounding), and |wdiff|^2 <= 1/4 implies
+// |delw|^2 >= 4|w|^2 > TOL_ZERO.
+constexpr double kFastWabs2Lo = 1.0e-12;
+constexpr double kFastWabs2Hi = 62499.0;
+
+constexpr int kMaxNw = 8;
+
+// Ordering of non-negative doubles equals the ordering of their bit patterns as signed
+// 64-bit integers. The comparisons below run on the integer pipe instead of the FP64 pipe
+// (on GB300 the FP64 pipe is the bottleneck of the whole sum). Arguments are >= +0 or NaN.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ bool gt_nonneg(double a, double b) { return dbits(a) > dbits(b); }
+__device__ __forceinline__ bool lt_nonneg(double a, double b) { return dbits(a) < dbits(b); }
+
+// FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined by one
+// third-order Householder step of Newton's reciprocal iteration,
+//   e = 1 - d*y,   y' = y * (1 + e + e^2),
+// whose relative error is e^3 plus rounding. Three FP64 FMAs instead of the longer
+// correctly-rounded sequence; the result differs from 1/d by a few ulp at most (checked
+// against 1.0/d by the test suite). d must be a normal, finite, non-zero double.
+__device__ __forceinline__ double rcp_approx(double d) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+  return y;
+}
+
+__device__ __forceinline__ double rcp_refined(double d) {
+  double y = rcp_approx(d);
+  double e = fma(-d, y, 1.0);
+  double q = fma(e, e, e);
+  return fma(y, q, y);
+}
+
+__device__ __forceinline__ double2 ldg2(const double2* p) { return __ldg(p); }
+
+// Sum of v over the warp by a fixed xor butterfly; lane 0's result is deterministic.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Per-CTA partial of NV doubles: warp butterflies, then warp partials summed in warp
+// order by the first NV threads. `red` is shared memory of at least (blockDim/32) * NV.
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&acc)[NV], double* red, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) red[warp * NV + k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) s += red[w * NV + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+}  // namespace gpp

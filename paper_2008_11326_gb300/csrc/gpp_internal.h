@@ -1,0 +1,49 @@
+// Host-side interface between the C-ABI layer (gpp_api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "gpp.h"
+
+namespace gpp {
+
+// Layout of the caller's workspace for one forward call. Every segment starts on a
+// 256-byte boundary.
+struct FwdPlan {
+  int threads = 128;      // threads per CTA of the main kernel
+  int grid = 0;           // CTAs of the main kernel (a persistent, statically scheduled grid)
+  int nw = 0;
+  int64_t n_ig_tiles = 0; // ig tiles of `threads` G-vectors per column
+  int64_t ntiles = 0;     // ngpown * n_ig_tiles
+  size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count
+  size_t off_colvalid = 0;// int32[P]
+  size_t off_bt = 0;      // band table double4[B][W] = {x, x^2, 4x, 0}
+  size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
+  size_t off_partials = 0;// double[grid][4 W]
+  size_t total = 0;
+};
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Main-kernel CTAs that fit on one SM (occupancy query; 0 on error).
+int fwd_f64_blocks_per_sm(int threads, int nw);
+int fwd_f32_blocks_per_sm(int threads, int nw);
+bool fwd_f32_available();
+
+// Column gather, band table and index checks (one kernel).
+cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
+                        cudaStream_t s);
+// Main sum in FP64 (writes per-CTA partials).
+cudaError_t launch_fwd_f64(const gpp_problem& p, int occ_mode, const FwdPlan& plan, char* ws,
+                           cudaStream_t s);
+// Main sum with FP32 bulk arithmetic (writes per-CTA partials in FP64).
+cudaError_t launch_fwd_f32(const gpp_problem& p, int occ_mode, const FwdPlan& plan, char* ws,
+                           cudaStream_t s);
+// Fixed-order reduction of the partials into achtemp / asxtemp.
+cudaError_t launch_reduce_final(const FwdPlan& plan, char* ws, gpp_c128* ach, gpp_c128* asx,
+                                cudaStream_t s);
+
+}  // namespace gpp

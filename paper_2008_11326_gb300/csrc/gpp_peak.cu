@@ -1,0 +1,92 @@
+// Throughput kernels for the FP64 / FP32 peaks and the reciprocal check (gpp_diag.h).
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "gpp_device.cuh"
+#include "gpp_diag.h"
+#include "gpp.h"
+
+namespace {
+
+constexpr int kChains = GPP_PEAK_CHAINS;
+
+template <int KIND>
+__device__ __forceinline__ double step(double a, double b, double c) {
+  if (KIND == GPP_PEAK_DFMA) return fma(a, b, c);
+  if (KIND == GPP_PEAK_DADD) return a + c;
+  if (KIND == GPP_PEAK_DMUL) return a * b;
+  if (KIND == GPP_PEAK_DRCP) return gpp::rcp_refined(a);
+  return __drcp_rn(a);
+}
+
+template <int KIND>
+__global__ void peak_f64_kernel(int64_t iters, double* sink) {
+  double v[kChains];
+  const double b = 1.0 - 1e-9 * (threadIdx.x & 7);
+  const double c = 1e-12 * (threadIdx.x + 1);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) v[k] = 1.0 + 1e-3 * k + 1e-7 * threadIdx.x;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) v[k] = step<KIND>(v[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += v[k];
+  if (s == 123.456789) *sink = s;
+}
+
+__global__ void peak_ffma_kernel(int64_t iters, double* sink) {
+  float v[kChains];
+  const float b = 1.0f - 1e-6f * (threadIdx.x & 7);
+  const float c = 1e-7f * (threadIdx.x + 1);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) v[k] = 1.0f + 1e-3f * k;
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) v[k] = fmaf(v[k], b, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += v[k];
+  if (s == 123.456789f) *sink = s;
+}
+
+__global__ void diag_rcp_kernel(const double* in, double* out, int64_t n) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = gpp::rcp_refined(in[i]);
+}
+
+thread_local std::string g_diag_err;
+
+}  // namespace
+
+extern "C" int gpp_peak_launch(int kind, int64_t iters, int blocks, int threads, double* sink,
+                               void* stream) {
+  if (!sink) return GPP_ERR_NULL_PTR;
+  if (iters < 0 || blocks < 1 || threads < 32 || threads > 1024) return GPP_ERR_BAD_SIZE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (kind) {
+    case GPP_PEAK_DFMA: peak_f64_kernel<GPP_PEAK_DFMA><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_FFMA: peak_ffma_kernel<<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_DADD: peak_f64_kernel<GPP_PEAK_DADD><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_DMUL: peak_f64_kernel<GPP_PEAK_DMUL><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_DRCP: peak_f64_kernel<GPP_PEAK_DRCP><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_DRCP_RN: peak_f64_kernel<GPP_PEAK_DRCP_RN><<<blocks, threads, 0, s>>>(iters, sink); break;
+    default: return GPP_ERR_BAD_OPTION;
+  }
+  return cudaGetLastError() == cudaSuccess ? GPP_OK : GPP_ERR_CUDA;
+}
+
+extern "C" int gpp_diag_rcp(const double* in, double* out, int64_t n, void* stream) {
+  if (n < 0) return GPP_ERR_BAD_SIZE;
+  if (n == 0) return GPP_OK;
+  if (!in || !out) return GPP_ERR_NULL_PTR;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  diag_rcp_kernel<<<static_cast<int>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
+  return cudaGetLastError() == cudaSuccess ? GPP_OK : GPP_ERR_CUDA;
+}

@@ -1,0 +1,186 @@
+"""Python face of libgpp: the GPP self-energy summation on one GB300.
+
+PyTorch supplies device memory and streams; every step of the sum runs in libgpp's CUDA
+kernels through the C-ABI (``include/gpp.h``). Names follow the paper's kernel.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+PRECISIONS = {"fp64": N.GPP_FP64, "fp32_bulk": N.GPP_FP32_BULK}
+OCC_MODES = {"all": N.GPP_OCC_ALL, "occupied": N.GPP_OCC_OCCUPIED}
+
+_C128 = ("aqsmtemp", "aqsntemp", "I_eps_array", "wtilde_array")
+
+
+@dataclasses.dataclass
+class DeviceProblem:
+    """Device tensors of one GPP instance (layouts as in include/gpp.h)."""
+
+    number_bands: int
+    nvband: int
+    ncouls: int
+    ngpown: int
+    nw: int
+    aqsmtemp: torch.Tensor      # complex128 [B][G]
+    aqsntemp: torch.Tensor      # complex128 [B][G]
+    I_eps_array: torch.Tensor   # complex128 [P][G]
+    wtilde_array: torch.Tensor  # complex128 [P][G]
+    vcoul: torch.Tensor         # float64 [G]
+    inv_igp_index: torch.Tensor  # int32 [P]
+    indinv: torch.Tensor        # int32 [G+1]
+    wx_array: torch.Tensor      # float64 [B][W]
+    aqsntemp_c64: torch.Tensor | None = None     # complex64 copies for fp32_bulk
+    I_eps_array_c64: torch.Tensor | None = None
+    wtilde_array_c64: torch.Tensor | None = None
+    aqsmtemp_c64: torch.Tensor | None = None
+
+    @classmethod
+    def from_host(cls, prob, device="cuda", c64: bool = False, pin: bool = False):
+        """Copy a host :class:`inputs.GppProblem` to ``device`` (or to pinned host memory
+        when ``device == 'cpu'`` and ``pin``)."""
+        def t(a, dt):
+            x = torch.from_numpy(np.ascontiguousarray(a)).to(dt)
+            if device == "cpu":
+                return x.pin_memory() if pin else x
+            return x.to(device)
+        kw = dict(number_bands=prob.number_bands, nvband=prob.nvband, ncouls=prob.ncouls,
+                  ngpown=prob.ngpown, nw=prob.nw)
+        for f in _C128:
+            kw[f] = t(getattr(prob, f), torch.complex128)
+        kw["vcoul"] = t(prob.vcoul, torch.float64)
+        kw["inv_igp_index"] = t(prob.inv_igp_index, torch.int32)
+        kw["indinv"] = t(prob.indinv, torch.int32)
+        kw["wx_array"] = t(prob.wx_array, torch.float64)
+        dp = cls(**kw)
+        if c64:
+            dp.make_c64()
+        return dp
+
+    def make_c64(self):
+        """complex64 copies of the complex arrays (for precision='fp32_bulk')."""
+        self.aqsmtemp_c64 = self.aqsmtemp.to(torch.complex64)
+        self.aqsntemp_c64 = self.aqsntemp.to(torch.complex64)
+        self.I_eps_array_c64 = self.I_eps_array.to(torch.complex64)
+        self.wtilde_array_c64 = self.wtilde_array.to(torch.complex64)
+        return self
+
+    @property
+    def device(self):
+        return self.aqsmtemp.device
+
+    def struct(self, ach: torch.Tensor, asx: torch.Tensor) -> N.GppProblem:
+        def ptr(x):
+            return None if x is None else x.data_ptr()
+        for f in _C128 + ("vcoul", "inv_igp_index", "indinv", "wx_array"):
+            x = getattr(self, f)
+            if not x.is_contiguous():
+                raise ValueError(f"{f} must be contiguous")
+        return N.GppProblem(
+            self.number_bands, self.nvband, self.ncouls, self.ngpown, self.nw,
+            ptr(self.aqsmtemp), ptr(self.aqsntemp), ptr(self.I_eps_array),
+            ptr(self.wtilde_array), ptr(self.vcoul), ptr(self.inv_igp_index), ptr(self.indinv),
+            ptr(self.wx_array), ptr(self.aqsmtemp_c64), ptr(self.aqsntemp_c64),
+            ptr(self.I_eps_array_c64), ptr(self.wtilde_array_c64), ptr(ach), ptr(asx))
+
+
+def _stream_handle(stream, device):
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_options(precision="fp64", occ_mode="all", block_threads=0, blocks_per_sm=0,
+                 debug_checks=False, stage_events=None) -> N.GppOptions:
+    """``stage_events``: four recorded ``torch.cuda.Event(enable_timing=True)`` (or raw
+    cudaEvent_t handles) that the call re-records around its stages (see gpp_options)."""
+    if stage_events is not None:
+        stage_events = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in stage_events]
+    return N.options(PRECISIONS[precision], OCC_MODES[occ_mode], block_threads, blocks_per_sm,
+                     debug_checks, stage_events)
+
+
+def workspace_size(dp: DeviceProblem, **opts) -> int:
+    o = make_options(**opts)
+    prob = dp.struct(None, None)
+    n = N.lib().gpp_sigma_workspace_size(ctypes.byref(prob), ctypes.byref(o))
+    err = N.lib().gpp_last_error().decode()
+    if n == 0 and err:
+        raise N.GppError(-2, err)
+    return int(n)
+
+
+def sigma(dp: DeviceProblem, *, out=None, workspace: torch.Tensor | None = None,
+          stream: torch.cuda.Stream | None = None, **opts):
+    """achtemp, asxtemp (complex128 [nw] device tensors) of one instance.
+
+    Enqueued on ``stream`` (default: torch's current stream) without synchronising.
+    ``opts``: precision ('fp64' | 'fp32_bulk'), occ_mode ('all' | 'occupied'),
+    block_threads, blocks_per_sm, debug_checks.
+    """
+    dev = dp.device
+    if out is None:
+        ach = torch.empty(dp.nw, dtype=torch.complex128, device=dev)
+        asx = torch.empty(dp.nw, dtype=torch.complex128, device=dev)
+    else:
+        ach, asx = out
+    o = make_options(**opts)
+    prob = dp.struct(ach, asx)
+    lib = N.lib()
+    need = lib.gpp_sigma_workspace_size(ctypes.byref(prob), ctypes.byref(o))
+    if need == 0 and lib.gpp_last_error():
+        raise N.GppError(-2, lib.gpp_last_error().decode())
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    N.check(lib.gpp_sigma(ctypes.byref(prob), ctypes.byref(o), ctypes.c_void_p(workspace.data_ptr()),
+                          workspace.numel(), _stream_handle(stream, dev)))
+    return ach, asx
+
+
+def host_workspace_size(hp: DeviceProblem, **opts) -> int:
+    o = make_options(**opts)
+    prob = hp.struct(None, None)
+    return int(N.lib().gpp_sigma_host_workspace_size(ctypes.byref(prob), ctypes.byref(o)))
+
+
+def sigma_host(hp: DeviceProblem, *, workspace: torch.Tensor, out=None,
+               stream: torch.cuda.Stream | None = None, **opts):
+    """The sum on HOST tensors (ideally pinned): copies in, computes, copies the outputs
+    back into host tensors and synchronises. ``workspace`` is a CUDA uint8 tensor of at
+    least :func:`host_workspace_size` bytes."""
+    if out is None:
+        ach = torch.empty(hp.nw, dtype=torch.complex128).pin_memory()
+        asx = torch.empty(hp.nw, dtype=torch.complex128).pin_memory()
+    else:
+        ach, asx = out
+    o = make_options(**opts)
+    prob = hp.struct(ach, asx)
+    N.check(N.lib().gpp_sigma_host(ctypes.byref(prob), ctypes.byref(o),
+                                   ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                   _stream_handle(stream, workspace.device)))
+    return ach, asx
+
+
+def peak_launch(kind: str, iters: int, blocks: int, threads: int, sink: torch.Tensor,
+                stream=None) -> float:
+    """Launch one throughput kernel; returns its operation count (see gpp_diag.h)."""
+    N.check(N.lib().gpp_peak_launch(N.PEAK_KINDS[kind], iters, blocks, threads,
+                                    ctypes.c_void_p(sink.data_ptr()),
+                                    _stream_handle(stream, sink.device)))
+    return float(blocks) * threads * N.PEAK_CHAINS * iters
+
+
+def rcp(x: torch.Tensor) -> torch.Tensor:
+    """The FP64 reciprocal the kernels use, applied elementwise (diagnostics)."""
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    N.check(N.lib().gpp_diag_rcp(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 x.numel(), _stream_handle(None, x.device)))
+    return out
