@@ -65,7 +65,9 @@ typedef enum gpp_status {
 
 typedef enum gpp_precision {
     GPP_FP64 = 0,      /* every step in FP64 */
-    GPP_FP32_BULK = 1  /* FP32 complex arithmetic on complex64 copies, FP64 where it matters */
+    GPP_FP32_BULK = 1  /* FP32 complex arithmetic (complex64 aqsntemp copy), FP64 branch
+                          decisions near the threshold, FP64 near the wdiff pole, compensated
+                          FP32 accumulation folded into FP64 reductions */
 } gpp_precision;
 
 typedef enum gpp_occ_mode {
@@ -98,11 +100,11 @@ typedef struct gpp_problem {
     const int32_t *inv_igp_index; /* [P] */
     const int32_t *indinv;        /* [G + 1] */
     const double *wx_array;       /* [B][W] */
-    /* complex64 copies, read by GPP_FP32_BULK (NULL otherwise) */
-    const gpp_c64 *aqsmtemp_c64;     /* [B][G] */
-    const gpp_c64 *aqsntemp_c64;     /* [B][G] */
-    const gpp_c64 *I_eps_array_c64;  /* [P][G] */
-    const gpp_c64 *wtilde_array_c64; /* [P][G] */
+    /* complex64 copy of aqsntemp, read by GPP_FP32_BULK for its per-band loads (NULL
+     * otherwise). The (igp, ig) arrays are read once per pair in FP64 and rounded in
+     * registers, and the gathered weights are rounded by the gather kernel, so no other
+     * copies are needed. */
+    const gpp_c64 *aqsntemp_c64; /* [B][G] */
     gpp_c128 *achtemp; /* [W] output */
     gpp_c128 *asxtemp; /* [W] output */
 } gpp_problem;

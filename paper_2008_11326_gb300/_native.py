@@ -34,9 +34,7 @@ class GppProblem(ctypes.Structure):
                 ("aqsmtemp", _vp), ("aqsntemp", _vp), ("I_eps_array", _vp),
                 ("wtilde_array", _vp), ("vcoul", _vp), ("inv_igp_index", _vp), ("indinv", _vp),
                 ("wx_array", _vp),
-                ("aqsmtemp_c64", _vp), ("aqsntemp_c64", _vp), ("I_eps_array_c64", _vp),
-                ("wtilde_array_c64", _vp),
-                ("achtemp", _vp), ("asxtemp", _vp)]
+                ("aqsntemp_c64", _vp), ("achtemp", _vp), ("asxtemp", _vp)]
 
 
 class GppOptions(ctypes.Structure):

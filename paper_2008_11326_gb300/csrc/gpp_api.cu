@@ -92,12 +92,8 @@ int check_pointers(const gpp_problem& p, int precision) {
     if (!aligned(r.ptr, r.align)) return fail(GPP_ERR_NULL_PTR, "%s is not %zu-byte aligned", r.name, r.align);
   }
   if (precision == GPP_FP32_BULK) {
-    const void* c64[] = {p.aqsntemp_c64, p.I_eps_array_c64, p.wtilde_array_c64};
-    const char* names[] = {"aqsntemp_c64", "I_eps_array_c64", "wtilde_array_c64"};
-    for (int i = 0; i < 3; ++i) {
-      if (!c64[i]) return fail(GPP_ERR_NULL_PTR, "%s is NULL (GPP_FP32_BULK)", names[i]);
-      if (!aligned(c64[i], 8)) return fail(GPP_ERR_NULL_PTR, "%s is not 8-byte aligned", names[i]);
-    }
+    if (!p.aqsntemp_c64) return fail(GPP_ERR_NULL_PTR, "aqsntemp_c64 is NULL (GPP_FP32_BULK)");
+    if (!aligned(p.aqsntemp_c64, 8)) return fail(GPP_ERR_NULL_PTR, "aqsntemp_c64 is not 8-byte aligned");
   }
   return GPP_OK;
 }
@@ -137,6 +133,12 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan) {
   off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(double));
   pl.off_partials = off;
   off = gpp::align_up(off + static_cast<size_t>(pl.grid) * 4 * p.nw * sizeof(double));
+  if (o.precision == GPP_FP32_BULK) {
+    pl.off_bt32 = off;
+    off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 32);
+    pl.off_am32 = off;
+    off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(float));
+  }
   pl.total = off;
   *plan = pl;
   return GPP_OK;
@@ -242,14 +244,13 @@ struct HostLayout {
   size_t total;
 };
 
-// Segment order: aqsm, aqsn, eps, wt, vcoul, inv, indinv, wx, aqsn_c64, eps_c64, wt_c64,
+// Segment order: aqsm, aqsn, eps, wt, vcoul, inv, indinv, wx, aqsn_c64, (two unused),
 // outputs (ach then asx).
 void host_layout(const gpp_problem& p, int precision, size_t sigma_bytes, HostLayout* L) {
   const size_t B = p.number_bands, G = p.ncouls, P = p.ngpown, W = p.nw;
   const bool f32 = precision == GPP_FP32_BULK;
   size_t sizes[12] = {B * G * 16, B * G * 16, P * G * 16, P * G * 16, G * 8, P * 4, (G + 1) * 4,
-                      B * W * 8,  f32 ? B * G * 8 : 0, f32 ? P * G * 8 : 0, f32 ? P * G * 8 : 0,
-                      2 * W * 16};
+                      B * W * 8,  f32 ? B * G * 8 : 0, 0, 0, 2 * W * 16};
   size_t off = 0;
   for (int i = 0; i < 12; ++i) {
     L->off[i] = off;
@@ -303,8 +304,8 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
                 {h.indinv, (G + 1) * 4, 6},
                 {h.wx_array, B * W * 8, 7},
                 {f32 ? h.aqsntemp_c64 : nullptr, B * G * 8, 8},
-                {f32 ? h.I_eps_array_c64 : nullptr, P * G * 8, 9},
-                {f32 ? h.wtilde_array_c64 : nullptr, P * G * 8, 10}};
+                {nullptr, 0, 9},
+                {nullptr, 0, 10}};
   gpp_problem d = h;
   void* dptr[11];
   for (int i = 0; i < 11; ++i) {
@@ -322,10 +323,7 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   d.inv_igp_index = static_cast<const int32_t*>(dptr[5]);
   d.indinv = static_cast<const int32_t*>(dptr[6]);
   d.wx_array = static_cast<const double*>(dptr[7]);
-  d.aqsmtemp_c64 = nullptr;
   d.aqsntemp_c64 = f32 ? static_cast<const gpp_c64*>(dptr[8]) : nullptr;
-  d.I_eps_array_c64 = f32 ? static_cast<const gpp_c64*>(dptr[9]) : nullptr;
-  d.wtilde_array_c64 = f32 ? static_cast<const gpp_c64*>(dptr[10]) : nullptr;
   d.achtemp = reinterpret_cast<gpp_c128*>(ws + L.off[11]);
   d.asxtemp = d.achtemp + W;
   rc = gpp_sigma(&d, &o, ws + L.sigma_off, L.total - L.sigma_off, stream);

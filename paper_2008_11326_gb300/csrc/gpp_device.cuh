@@ -24,6 +24,26 @@ constexpr double kFastWabs2Hi = 62499.0;
 
 constexpr int kMaxNw = 8;
 
+// One (band, iw) entry of the FP64 band table: x = wx_array[b][iw], x^2, 4x, -x/2.
+struct alignas(32) BandEntry {
+  double2 lo;  // x, x^2
+  double2 hi;  // 4x, -x/2
+};
+
+// The FP32 band table entry: x, x^2, 4x, -x/2 rounded to FP32, and the part of the
+// branch-decision margin that depends on x (see gpp_fwd_f32.cu).
+struct alignas(32) BandEntry32 {
+  float4 a;  // x, x^2, 4x, -x/2
+  float4 b;  // margin_x, 0, 0, 0
+};
+
+// Flags written by the gather kernel: [0] some wx < 0 or NaN, [1] bad index count,
+// [2] some |wx| >= kFp32MaxX or NaN (the FP32 decision margin assumes smaller x).
+constexpr double kFp32MaxX = 1.0e4;
+
+// Scale of the FP32 branch-decision margin, 2^-20 (see gpp_fwd_f32.cu).
+constexpr float kMarginScale = 9.5367431640625e-07f;
+
 // Ordering of non-negative doubles equals the ordering of their bit patterns as signed
 // 64-bit integers. The comparisons below run on the integer pipe instead of the FP64 pipe
 // (on GB300 the FP64 pipe is the bottleneck of the whole sum). Arguments are >= +0 or NaN.

@@ -23,16 +23,12 @@
 
 #include "gpp_device.cuh"
 #include "gpp_internal.h"
+#include "gpp_terms_f64.cuh"
 
 namespace gpp {
 
 namespace {
 
-// One (band, iw) entry of the band table: x = wx_array[b][iw], x^2, 4x. 32-byte aligned.
-struct alignas(32) BandEntry {
-  double2 lo;  // x, x^2
-  double2 hi;  // 4x, 0
-};
 
 // Global column of local column p, or -1 if it contributes nothing. Counts indices that
 // are outside their arrays (the sentinel indinv[k] == G is legitimate).
@@ -52,14 +48,14 @@ __device__ __forceinline__ int column_of(int64_t p, int64_t G, const int32_t* in
 }
 
 // Column gather (paper §III v7: aqsmtemp_local(igp, band) stored band-contiguous),
-// band table and index checks.
+// band tables and index checks. am32 / bt32 (the FP32-bulk copies) may be NULL.
 __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
                                 const double2* __restrict__ aqsm,
                                 const double* __restrict__ vcoul,
                                 const int32_t* __restrict__ inv,
                                 const int32_t* __restrict__ indinv,
                                 const double* __restrict__ wx, int* flags, int* colg,
-                                BandEntry* bt, double2* am) {
+                                BandEntry* bt, double2* am, BandEntry32* bt32, float2* am32) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   for (int64_t p = tid; p < P; p += stride) colg[p] = column_of(p, G, inv, indinv, flags + 1);
@@ -73,92 +69,20 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
       v = make_double2(m.x * vc, -m.y * vc);
     }
     am[i] = v;
+    if (am32) am32[i] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
   }
   for (int64_t i = tid; i < B * W; i += stride) {
     double x = wx[i];
-    bt[i] = BandEntry{make_double2(x, x * x), make_double2(4.0 * x, 0.0)};
+    bt[i] = BandEntry{make_double2(x, x * x), make_double2(4.0 * x, -0.5 * x)};
     if (!(x >= 0.0)) flags[0] = 1;
-  }
-}
-
-// One band's contribution for the thread's (p, ig) pair, all frequencies.
-// FAST: every lane of the warp has 1e-12 < |w|^2 < 62499 and Re w >= 0, and every wx is
-// >= 0: branch 1 is exactly |wdiff|^2 > 1/4 and |S|^2 = |A|^2 + 4 x Re(w) has no
-// cancellation. Otherwise the general form evaluates both thresholds and forms S directly.
-template <int W, bool FAST>
-__device__ __forceinline__ void band_terms(double Kr, double Ki, double K2r, double K2i,
-                                           bool occ, const BandEntry* __restrict__ btb,
-                                           double wr, double wi, double wi2, double wabs2,
-                                           double w2r, double w2i, double (&acc)[4 * W]) {
-  const double Khr = -0.5 * Kr, Khi = -0.5 * Ki;
-#pragma unroll
-  for (int iw = 0; iw < W; ++iw) {
-    const double2 xlo = __ldg(&btb[iw].lo);
-    const double x = xlo.x, x2 = xlo.y, x4 = __ldg(&btb[iw].hi.x);
-    const double Ar = x - wr;                 // A = x - w = (Ar, -wi)
-    const double A2 = fma(Ar, Ar, wi2);       // |wdiff|^2
-    double S2, Sr = 0.0;
-    bool c1, c2;
-    if (FAST) {
-      S2 = fma(x4, wr, A2);                   // |x + w|^2
-      c1 = gt_nonneg(A2, kLimitTwo);
-      c2 = true;
-    } else {
-      Sr = x + wr;
-      S2 = fma(Sr, Sr, wi2);
-      // |delw|^2 = |w|^2 / |wdiff|^2 compared through products (A2 > 0)
-      c1 = gt_nonneg(A2, kLimitTwo) && lt_nonneg(wabs2, kLimitOne * A2);
-      c2 = gt_nonneg(wabs2, kTolZero * A2);
+    if (!(fabs(x) < kFp32MaxX)) flags[2] = 1;
+    if (bt32) {
+      const float xf = static_cast<float>(x);
+      BandEntry32 e;
+      e.a = make_float4(xf, static_cast<float>(x * x), 4.0f * xf, -0.5f * xf);
+      e.b = make_float4(kMarginScale * (fabsf(xf) + 2.0f), 0.0f, 0.0f, 0.0f);
+      bt32[i] = e;
     }
-    const double r = rcp_refined(A2 * S2);
-    // achtemp: branch 1 only, K conj(A) / |A|^2 with conj(A) = (Ar, wi)
-    const double a1 = c1 ? S2 * r : 0.0;
-    const double tr = fma(Kr, Ar, -Ki * wi);
-    const double ti = fma(Ki, Ar, Kr * wi);
-    acc[4 * iw + 0] = fma(tr, a1, acc[4 * iw + 0]);
-    acc[4 * iw + 1] = fma(ti, a1, acc[4 * iw + 1]);
-    if (occ) {
-      // asxtemp: branch 1 -> K2 conj(C) r with conj(C) = (x^2 - Re w^2, Im w^2);
-      //          branch 2 -> (-K/2) conj(S) |A|^2 r with conj(S) = (x + Re w, -Im w)
-      const double b2 = A2 * r;
-      const double coef = c1 ? r : (c2 ? b2 : 0.0);
-      const double Zr = c1 ? K2r : Khr;
-      const double Zi = c1 ? K2i : Khi;
-      const double Yr = FAST ? (c1 ? x2 : x) + (c1 ? -w2r : wr) : (c1 ? x2 - w2r : Sr);
-      const double Yi = c1 ? w2i : -wi;
-      const double ur = fma(Zr, Yr, -Zi * Yi);
-      const double ui = fma(Zi, Yr, Zr * Yi);
-      acc[4 * iw + 2] = fma(ur, coef, acc[4 * iw + 2]);
-      acc[4 * iw + 3] = fma(ui, coef, acc[4 * iw + 3]);
-    }
-  }
-}
-
-template <int W, bool FAST>
-__device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
-                                          const double2* __restrict__ an_ptr,
-                                          const double2* __restrict__ am_ptr,
-                                          const BandEntry* __restrict__ bt, bool live,
-                                          double wr, double wi, double Iwr, double Iwi,
-                                          double (&acc)[4 * W]) {
-  const double wi2 = wi * wi;
-  const double wabs2 = fma(wr, wr, wi2);
-  const double w2r = fma(wr, wr, -wi2);
-  const double w2i = 2.0 * wr * wi;
-#pragma unroll 1
-  for (int b = 0; b < B; ++b) {
-    const double2 an = live ? ldg2(an_ptr) : make_double2(0.0, 0.0);
-    an_ptr += G;
-    const double2 am = ldg2(am_ptr + b);
-    // M = am * an with am = conj(aqsmtemp[b][g]) vcoul[g]; K = M I w; K2 = K w
-    const double Mr = fma(am.x, an.x, -am.y * an.y);
-    const double Mi = fma(am.x, an.y, am.y * an.x);
-    const double Kr = fma(Mr, Iwr, -Mi * Iwi);
-    const double Ki = fma(Mr, Iwi, Mi * Iwr);
-    const double K2r = fma(Kr, wr, -Ki * wi);
-    const double K2i = fma(Kr, wi, Ki * wr);
-    band_terms<W, FAST>(Kr, Ki, K2r, K2i, b < nocc, bt + static_cast<int64_t>(b) * W, wr, wi,
-                        wi2, wabs2, w2r, w2i, acc);
   }
 }
 
@@ -272,7 +196,7 @@ int fwd_f64_blocks_per_sm(int threads, int nw) {
   return n;
 }
 
-cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool /*fp32*/,
+cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
                         cudaStream_t s) {
   int* flags = reinterpret_cast<int*>(ws + plan.off_flags);
   cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
@@ -285,7 +209,9 @@ cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, boo
       p.number_bands, p.ncouls, p.ngpown, static_cast<int>(p.nw),
       reinterpret_cast<const double2*>(p.aqsmtemp), p.vcoul, p.inv_igp_index, p.indinv,
       p.wx_array, flags, reinterpret_cast<int*>(ws + plan.off_colvalid),
-      reinterpret_cast<BandEntry*>(ws + plan.off_bt), reinterpret_cast<double2*>(ws + plan.off_am));
+      reinterpret_cast<BandEntry*>(ws + plan.off_bt), reinterpret_cast<double2*>(ws + plan.off_am),
+      fp32 ? reinterpret_cast<BandEntry32*>(ws + plan.off_bt32) : nullptr,
+      fp32 ? reinterpret_cast<float2*>(ws + plan.off_am32) : nullptr);
   return cudaGetLastError();
 }
 

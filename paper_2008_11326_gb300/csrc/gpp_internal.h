@@ -17,11 +17,13 @@ struct FwdPlan {
   int nw = 0;
   int64_t n_ig_tiles = 0; // ig tiles of `threads` G-vectors per column
   int64_t ntiles = 0;     // ngpown * n_ig_tiles
-  size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count
+  size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count, [2] any |wx| >= 1e4
   size_t off_colvalid = 0;// int32[P]
   size_t off_bt = 0;      // band table double4[B][W] = {x, x^2, 4x, 0}
   size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
   size_t off_partials = 0;// double[grid][4 W]
+  size_t off_bt32 = 0;    // FP32-bulk only: BandEntry32[B][W]
+  size_t off_am32 = 0;    // FP32-bulk only: gathered weights c64[P][B]
   size_t total = 0;
 };
 

@@ -1,0 +1,107 @@
+// The FP64 per-band evaluation of the plasmon-pole terms, shared by the FP64 forward
+// kernel and the general-input path of the FP32-bulk kernel. The algebra is described at
+// the top of gpp_fwd.cu.
+#pragma once
+
+#include "gpp_device.cuh"
+
+namespace gpp {
+
+// One band's contribution for the thread's (p, ig) pair, all frequencies.
+// FAST: every lane of the warp has 1e-12 < |w|^2 < 62499 and Re w >= 0, and every wx is
+// >= 0: branch 1 is exactly |wdiff|^2 > 1/4 and |S|^2 = |A|^2 + 4 x Re(w) has no
+// cancellation. Otherwise the general form evaluates both thresholds and forms S directly.
+//
+// Per band the caller has formed K = M I w, K2 = K w and the cross terms that do not
+// depend on the frequency:
+//   Kw = (-Im K Im w, Re K Im w)     so that K conj(A) = (Re K Ar + Kw.re, Im K Ar + Kw.im)
+//   P1 = (-Im K2 Im w^2, Re K2 Im w^2)  so that K2 conj(C) = (Re K2 Yr + P1.re, Im K2 Yr + P1.im)
+//   P2 = Kw / 2                         so that K (-conj(S)/2) = (Re K Yr + P2.re, Im K Yr + P2.im)
+// with Yr = x^2 - Re w^2 (branch 1) or -(x + Re w)/2 (branch 2).
+struct BandK {
+  double Kr, Ki, K2r, K2i, Kwr, Kwi, P1r, P1i, P2r, P2i;
+};
+
+template <int W, bool FAST>
+__device__ __forceinline__ void band_terms(const BandK& k, bool occ,
+                                           const BandEntry* __restrict__ btb, double wr,
+                                           double wi2, double wabs2, double mw2r, double wrh,
+                                           double (&acc)[4 * W]) {
+#pragma unroll
+  for (int iw = 0; iw < W; ++iw) {
+    const double2 xlo = __ldg(&btb[iw].lo);
+    const double2 xhi = __ldg(&btb[iw].hi);
+    const double x = xlo.x, x2 = xlo.y, x4 = xhi.x, xh = xhi.y;
+    const double Ar = x - wr;                 // A = x - w = (Ar, -Im w)
+    const double A2 = fma(Ar, Ar, wi2);       // |wdiff|^2
+    double S2;
+    bool c1, c2;
+    if (FAST) {
+      S2 = fma(x4, wr, A2);                   // |x + w|^2
+      c1 = gt_nonneg(A2, kLimitTwo);
+      c2 = true;
+    } else {
+      const double Sr = x + wr;
+      S2 = fma(Sr, Sr, wi2);
+      // |delw|^2 = |w|^2 / |wdiff|^2 compared through products (A2 > 0)
+      c1 = gt_nonneg(A2, kLimitTwo) && lt_nonneg(wabs2, kLimitOne * A2);
+      c2 = gt_nonneg(wabs2, kTolZero * A2);
+    }
+    const double r = rcp_refined(A2 * S2);
+    // achtemp, branch 1 only: K conj(A) / |A|^2
+    const double a1 = c1 ? S2 * r : 0.0;
+    const double tr = fma(k.Kr, Ar, k.Kwr);
+    const double ti = fma(k.Ki, Ar, k.Kwi);
+    acc[4 * iw + 0] = fma(tr, a1, acc[4 * iw + 0]);
+    acc[4 * iw + 1] = fma(ti, a1, acc[4 * iw + 1]);
+    if (occ) {
+      // asxtemp: branch 1 -> K2 conj(C) / |C|^2,  branch 2 -> K (-conj(S)/2) / |S|^2
+      const double b2 = A2 * r;
+      const double coef = c1 ? r : (c2 ? b2 : 0.0);
+      const double Yr = (c1 ? x2 : xh) + (c1 ? mw2r : wrh);
+      const double ur = fma(c1 ? k.K2r : k.Kr, Yr, c1 ? k.P1r : k.P2r);
+      const double ui = fma(c1 ? k.K2i : k.Ki, Yr, c1 ? k.P1i : k.P2i);
+      acc[4 * iw + 2] = fma(ur, coef, acc[4 * iw + 2]);
+      acc[4 * iw + 3] = fma(ui, coef, acc[4 * iw + 3]);
+    }
+  }
+}
+
+template <int W, bool FAST>
+__device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
+                                          const double2* __restrict__ an_ptr,
+                                          const double2* __restrict__ am_ptr,
+                                          const BandEntry* __restrict__ bt, bool live,
+                                          double wr, double wi, double Iwr, double Iwi,
+                                          double (&acc)[4 * W]) {
+  const double wi2 = wi * wi;
+  const double wabs2 = fma(wr, wr, wi2);
+  const double mw2r = -fma(wr, wr, -wi2);   // -Re w^2
+  const double w2i = 2.0 * wr * wi;         // Im w^2
+  const double wrh = -0.5 * wr;
+  const double wih = 0.5 * wi;
+#pragma unroll 1
+  for (int b = 0; b < B; ++b) {
+    const double2 an = live ? ldg2(an_ptr) : make_double2(0.0, 0.0);
+    an_ptr += G;
+    const double2 am = ldg2(am_ptr + b);
+    BandK k;
+    // M = am * an with am = conj(aqsmtemp[b][g]) vcoul[g]; K = M I w; K2 = K w
+    const double Mr = fma(am.x, an.x, -am.y * an.y);
+    const double Mi = fma(am.x, an.y, am.y * an.x);
+    k.Kr = fma(Mr, Iwr, -Mi * Iwi);
+    k.Ki = fma(Mr, Iwi, Mi * Iwr);
+    k.K2r = fma(k.Kr, wr, -k.Ki * wi);
+    k.K2i = fma(k.Kr, wi, k.Ki * wr);
+    k.Kwr = -k.Ki * wi;
+    k.Kwi = k.Kr * wi;
+    k.P1r = -k.K2i * w2i;
+    k.P1i = k.K2r * w2i;
+    k.P2r = -k.Ki * wih;
+    k.P2i = k.Kr * wih;
+    band_terms<W, FAST>(k, b < nocc, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r,
+                        wrh, acc);
+  }
+}
+
+}  // namespace gpp

@@ -37,10 +37,7 @@ class DeviceProblem:
     inv_igp_index: torch.Tensor  # int32 [P]
     indinv: torch.Tensor        # int32 [G+1]
     wx_array: torch.Tensor      # float64 [B][W]
-    aqsntemp_c64: torch.Tensor | None = None     # complex64 copies for fp32_bulk
-    I_eps_array_c64: torch.Tensor | None = None
-    wtilde_array_c64: torch.Tensor | None = None
-    aqsmtemp_c64: torch.Tensor | None = None
+    aqsntemp_c64: torch.Tensor | None = None     # complex64 copy for fp32_bulk
 
     @classmethod
     def from_host(cls, prob, device="cuda", c64: bool = False, pin: bool = False):
@@ -65,11 +62,8 @@ class DeviceProblem:
         return dp
 
     def make_c64(self):
-        """complex64 copies of the complex arrays (for precision='fp32_bulk')."""
-        self.aqsmtemp_c64 = self.aqsmtemp.to(torch.complex64)
+        """The complex64 copy of aqsntemp that precision='fp32_bulk' reads per band."""
         self.aqsntemp_c64 = self.aqsntemp.to(torch.complex64)
-        self.I_eps_array_c64 = self.I_eps_array.to(torch.complex64)
-        self.wtilde_array_c64 = self.wtilde_array.to(torch.complex64)
         return self
 
     @property
@@ -87,8 +81,7 @@ class DeviceProblem:
             self.number_bands, self.nvband, self.ncouls, self.ngpown, self.nw,
             ptr(self.aqsmtemp), ptr(self.aqsntemp), ptr(self.I_eps_array),
             ptr(self.wtilde_array), ptr(self.vcoul), ptr(self.inv_igp_index), ptr(self.indinv),
-            ptr(self.wx_array), ptr(self.aqsmtemp_c64), ptr(self.aqsntemp_c64),
-            ptr(self.I_eps_array_c64), ptr(self.wtilde_array_c64), ptr(ach), ptr(asx))
+            ptr(self.wx_array), ptr(self.aqsntemp_c64), ptr(ach), ptr(asx))
 
 
 def _stream_handle(stream, device):

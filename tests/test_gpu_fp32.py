@@ -1,0 +1,108 @@
+"""GPU parity of the FP32-bulk forward (GPP_FP32_BULK) against the FP64 oracle.
+
+Target: relative error <= 1e-6 on each achtemp / asxtemp value.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_11326_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gpp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2008_11326_gb300 import gpp as g
+    return g
+
+
+def run(gpp, prob, precision="fp32_bulk", **opts):
+    import torch
+    dp = gpp.DeviceProblem.from_host(prob, device="cuda", c64=(precision == "fp32_bulk"))
+    ach, asx = gpp.sigma(dp, precision=precision, **opts)
+    torch.cuda.synchronize()
+    return ach.cpu().numpy(), asx.cpu().numpy()
+
+
+def rel_err(got, ref):
+    got = np.concatenate([np.ravel(g) for g in got])
+    ref = np.concatenate([np.ravel(r) for r in ref])
+    return float(np.max(np.abs(got - ref) / np.abs(ref)))
+
+
+def test_tiny(gpp):
+    prob = inputs.config("tiny")
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+
+
+@pytest.mark.parametrize("shape", [(5, 1000, 37, 3), (3, 129, 2, 8), (40, 700, 9, 1),
+                                   (70, 300, 4, 4)])
+def test_ragged_and_chunk_tails(gpp, shape):
+    B, G, P, W = shape
+    prob = inputs.make_problem(B, 2, G, P, W, seed=B + G)
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+
+
+def test_decisions_next_to_the_branch_threshold(gpp):
+    """Frequencies spread densely over the range of Re w put many terms within FP32
+    rounding of |wdiff| = 1/2; a wrong branch decision would cost ~1e-4 here."""
+    prob = inputs.make_problem(64, 2, 2048, 16, 3, seed=17)
+    wx = np.linspace(0.0, 3.6, 192).reshape(64, 3)
+    prob = prob.replace(wx_array=wx)
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+
+
+def test_next_to_the_wdiff_pole(gpp):
+    """Real w with frequencies 1e-9 away from Re w: |wdiff|^2 is 0 in FP32 and 1e-18 in
+    FP64. The branch-2 coefficient is taken in FP64 there; the result stays finite."""
+    prob = inputs.make_problem(6, 2, 256, 4, 3, seed=23)
+    wt = prob.wtilde_array.copy()
+    vals = np.array([0.75, 1.25, 2.0, 2.5])
+    wt[:, :64] = np.tile(vals, 16)[None, :] + 0j
+    wx = np.array([[0.75 + 1e-9, 1.25 + 1e-9, 5.0], [2.0 + 1e-9, 2.5 - 1e-9, 0.3],
+                   [1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [0.75 + 2e-9, 7.0, 8.0],
+                   [9.0, 2.5 + 3e-9, 1.25 - 1e-9]])
+    prob = prob.replace(wtilde_array=wt, wx_array=wx)
+    got = run(gpp, prob)
+    assert all(np.all(np.isfinite(g)) for g in got)
+    assert rel_err(got, oracle.sigma(prob)) <= RTOL
+
+
+def test_general_inputs_take_the_fp64_path(gpp):
+    prob = inputs.make_problem(6, 2, 200, 6, 4, seed=77)
+    wx = np.linspace(-2.5, 3.5, 24).reshape(6, 4)     # negative x
+    prob = prob.replace(wx_array=wx)
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= 1e-12
+
+
+def test_occupied_mode(gpp):
+    prob = inputs.make_problem(40, 2, 600, 7, 3, seed=9)
+    assert rel_err(run(gpp, prob, occ_mode="occupied"), oracle.sigma(prob, occ_mode=1)) <= RTOL
+
+
+def test_deterministic(gpp):
+    prob = inputs.make_problem(33, 2, 1024, 20, 3, seed=4)
+    a = run(gpp, prob)
+    b = run(gpp, prob)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_benchmark_shape_band_subset(gpp):
+    prob = inputs.config("mixed").bands(slice(0, 8))
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+
+
+def test_benchmark_shape_full_vs_fp64(gpp):
+    """Full mixed-precision workload (B=512, P=1638, G=32768, nw=3) against the FP64 GPU
+    path, which itself matches the oracle to 1e-12."""
+    prob = inputs.config("mixed")
+    f32 = run(gpp, prob)
+    f64 = run(gpp, prob, precision="fp64")
+    assert rel_err(f32, f64) <= RTOL
