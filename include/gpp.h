@@ -158,6 +158,33 @@ GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_
 GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void *workspace,
                    size_t workspace_bytes, void *stream);
 
+/* Gradients written by gpp_sigma_backward (device pointers; NULL skips that gradient). */
+typedef struct gpp_grads {
+    gpp_c128 *wtilde_array; /* [P][G] */
+    gpp_c128 *I_eps_array;  /* [P][G] */
+    gpp_c128 *aqsmtemp;     /* [B][G]; entries of global columns no igp reaches are 0 */
+    gpp_c128 *aqsntemp;     /* [B][G] */
+} gpp_grads;
+
+/* Workspace bytes gpp_sigma_backward needs (0 with gpp_last_error() set on bad input). */
+GPP_API size_t gpp_sigma_backward_workspace_size(const gpp_problem *prob, const gpp_options *opt);
+
+/*
+ * Adjoint of gpp_sigma in FP64 (a derivative of the sum that the paper does not treat).
+ * Given the cotangents of the outputs in PyTorch's convention for complex tensors,
+ * grad_achtemp[iw] = dL/dRe achtemp[iw] + i dL/dIm achtemp[iw] (likewise grad_asxtemp;
+ * device arrays of nw), writes dL/dRe z + i dL/dIm z for z = wtilde_array, I_eps_array,
+ * aqsmtemp, aqsntemp into `grads` (overwritten, not accumulated). Inside a branch every
+ * term is holomorphic in wtilde, I_eps and aqsntemp and anti-holomorphic in aqsmtemp;
+ * the branch predicates contribute no derivative. Terms are recomputed from the inputs,
+ * not stored. prob->achtemp / asxtemp are not used. opt->precision must be GPP_FP64.
+ * Asynchronous on `stream`; deterministic. Errors as gpp_sigma, plus UNSUPPORTED.
+ */
+GPP_API int gpp_sigma_backward(const gpp_problem *prob, const gpp_options *opt,
+                               const gpp_c128 *grad_achtemp, const gpp_c128 *grad_asxtemp,
+                               const gpp_grads *grads, void *workspace, size_t workspace_bytes,
+                               void *stream);
+
 /* Thread-local description of the last error on this host thread ("" if none). */
 GPP_API const char *gpp_last_error(void);
 

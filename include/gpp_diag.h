@@ -25,7 +25,12 @@ typedef enum gpp_peak_kind {
     GPP_PEAK_DADD = 2,    /* FP64 add chains (1 FLOP each) */
     GPP_PEAK_DMUL = 3,    /* FP64 multiply chains (1 FLOP each) */
     GPP_PEAK_DRCP = 4,    /* the sum's FP64 reciprocal: approximation + 3 FMA (1 op each) */
-    GPP_PEAK_DRCP_RN = 5  /* CUDA's correctly rounded FP64 reciprocal __drcp_rn (1 op each) */
+    GPP_PEAK_DRCP_RN = 5, /* CUDA's correctly rounded FP64 reciprocal __drcp_rn (1 op each) */
+    GPP_PEAK_DRCP_APPROX = 6, /* the hardware FP64 reciprocal approximation alone (1 op each) */
+    GPP_PEAK_FSEL = 7,    /* FP32 select on a data-dependent predicate (1 op each) */
+    GPP_PEAK_FSETP = 8,   /* FP32 compare feeding an integer select (1 op each) */
+    GPP_PEAK_ISEL = 9,    /* 32-bit integer select (1 op each) */
+    GPP_PEAK_F2F = 10     /* FP64 -> FP32 -> FP64 round trip (1 op each) */
 } gpp_peak_kind;
 
 /* Independent dependency chains per thread in every throughput kernel. */

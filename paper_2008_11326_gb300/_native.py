@@ -20,7 +20,8 @@ STATUS = {0: "GPP_OK", -1: "GPP_ERR_NULL_PTR", -2: "GPP_ERR_BAD_SIZE", -3: "GPP_
 GPP_FP64, GPP_FP32_BULK = 0, 1
 GPP_OCC_ALL, GPP_OCC_OCCUPIED = 0, 1
 GPP_MAX_NW = 8
-PEAK_KINDS = {"dfma": 0, "ffma": 1, "dadd": 2, "dmul": 3, "drcp": 4, "drcp_rn": 5}
+PEAK_KINDS = {"dfma": 0, "ffma": 1, "dadd": 2, "dmul": 3, "drcp": 4, "drcp_rn": 5,
+              "drcp_approx": 6, "fsel": 7, "fsetp": 8, "isel": 9, "f2f": 10}
 PEAK_CHAINS = 8
 
 _vp = ctypes.c_void_p
@@ -35,6 +36,11 @@ class GppProblem(ctypes.Structure):
                 ("wtilde_array", _vp), ("vcoul", _vp), ("inv_igp_index", _vp), ("indinv", _vp),
                 ("wx_array", _vp),
                 ("aqsntemp_c64", _vp), ("achtemp", _vp), ("asxtemp", _vp)]
+
+
+class GppGrads(ctypes.Structure):
+    _fields_ = [("wtilde_array", _vp), ("I_eps_array", _vp), ("aqsmtemp", _vp),
+                ("aqsntemp", _vp)]
 
 
 class GppOptions(ctypes.Structure):
@@ -54,6 +60,11 @@ SIGNATURES = [
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions)]),
     ("gpp_sigma_host", ctypes.c_int,
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions), _vp, ctypes.c_size_t, _vp]),
+    ("gpp_sigma_backward_workspace_size", ctypes.c_size_t,
+     [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions)]),
+    ("gpp_sigma_backward", ctypes.c_int,
+     [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions), _vp, _vp,
+      ctypes.POINTER(GppGrads), _vp, ctypes.c_size_t, _vp]),
     ("gpp_last_error", ctypes.c_char_p, []),
     ("gpp_version", ctypes.c_char_p, []),
     ("gpp_peak_launch", ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp]),

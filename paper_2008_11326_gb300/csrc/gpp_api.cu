@@ -74,10 +74,12 @@ int check_sizes(const gpp_problem& p) {
 }
 
 // Pointers the forward pass reads for this precision; complex arrays 16- or 8-byte aligned.
-int check_pointers(const gpp_problem& p, int precision) {
-  if (!p.achtemp || !p.asxtemp) return fail(GPP_ERR_NULL_PTR, "achtemp and asxtemp must be non-NULL");
-  if (!aligned(p.achtemp, 16) || !aligned(p.asxtemp, 16))
-    return fail(GPP_ERR_NULL_PTR, "achtemp / asxtemp must be 16-byte aligned");
+int check_pointers(const gpp_problem& p, int precision, bool outputs = true) {
+  if (outputs) {
+    if (!p.achtemp || !p.asxtemp) return fail(GPP_ERR_NULL_PTR, "achtemp and asxtemp must be non-NULL");
+    if (!aligned(p.achtemp, 16) || !aligned(p.asxtemp, 16))
+      return fail(GPP_ERR_NULL_PTR, "achtemp / asxtemp must be 16-byte aligned");
+  }
   if (degenerate(p)) return GPP_OK;
   struct {
     const void* ptr;
@@ -141,6 +143,50 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan) {
   }
   pl.total = off;
   *plan = pl;
+  return GPP_OK;
+}
+
+// Adjoint workspace: the gather segments of the forward layout (with a one-CTA partial
+// area), then the adjoint's band table, batch partials and per-(band, column) totals.
+constexpr size_t kBwdPartialBudget = size_t(1) << 30;  // bytes for the per-batch partials
+
+int make_bwd_plan(const gpp_problem& p, const gpp_options& o, gpp::BwdPlan* plan) {
+  gpp::BwdPlan bp;
+  gpp_options fo = o;
+  fo.precision = GPP_FP64;
+  fo.blocks_per_sm = 1;
+  int rc = make_plan(p, fo, &bp.fwd);
+  if (rc) return rc;
+  if (degenerate(p)) {
+    *plan = bp;
+    return GPP_OK;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+  const int bps = gpp::bwd_blocks_per_sm(static_cast<int>(p.nw));
+  if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for the adjoint kernel");
+  bp.max_grid = sms * bps;
+  const int64_t groups = gpp::bwd_groups(p.ngpown);
+  const size_t per_group = static_cast<size_t>(p.number_bands) * p.ncouls * 16;
+  int64_t bg = static_cast<int64_t>(kBwdPartialBudget / (per_group ? per_group : 1));
+  if (bg < 1) bg = 1;
+  if (bg > groups) bg = groups;
+  bp.batch_groups = static_cast<int>(bg);
+  const int64_t n_ig_tiles = (p.ncouls + gpp::bwd_tile_ig() - 1) / gpp::bwd_tile_ig();
+  size_t off = bp.fwd.total;
+  bp.off_bwd_bt = off;
+  off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 128);
+  bp.off_part_n = off;
+  off = gpp::align_up(off + static_cast<size_t>(bg) * per_group);
+  bp.off_part_r = off;
+  off = gpp::align_up(off + static_cast<size_t>(n_ig_tiles) * p.number_bands * bg *
+                                gpp::bwd_tile_cols() * 16);
+  bp.off_rtot = off;
+  off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.ngpown * 16);
+  bp.total = off;
+  *plan = bp;
   return GPP_OK;
 }
 
@@ -228,6 +274,67 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "running the sum");
   }
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+size_t gpp_sigma_backward_workspace_size(const gpp_problem* prob, const gpp_options* opt) {
+  gpp_options o;
+  if (validate(prob, opt, &o)) return 0;
+  gpp::BwdPlan plan;
+  if (make_bwd_plan(*prob, o, &plan)) return 0;
+  g_last_error.clear();
+  return plan.total;
+}
+
+int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
+                       const gpp_c128* grad_achtemp, const gpp_c128* grad_asxtemp,
+                       const gpp_grads* grads, void* workspace, size_t workspace_bytes,
+                       void* stream) {
+  gpp_options o;
+  int rc = validate(prob, opt, &o);
+  if (rc) return rc;
+  if (o.precision != GPP_FP64)
+    return fail(GPP_ERR_UNSUPPORTED, "the adjoint is implemented in FP64 only");
+  if (!grads) return fail(GPP_ERR_NULL_PTR, "grads is NULL");
+  const gpp_problem& p = *prob;
+  if ((rc = check_pointers(p, GPP_FP64, false))) return rc;
+  if (!grad_achtemp || !grad_asxtemp) return fail(GPP_ERR_NULL_PTR, "output cotangents are NULL");
+  gpp_c128* outs[4] = {grads->wtilde_array, grads->I_eps_array, grads->aqsmtemp, grads->aqsntemp};
+  for (auto* q : outs)
+    if (q && !aligned(q, 16)) return fail(GPP_ERR_NULL_PTR, "gradient arrays must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (degenerate(p)) {
+    const size_t pg = static_cast<size_t>(p.ngpown) * p.ncouls * 16;
+    const size_t bg = static_cast<size_t>(p.number_bands) * p.ncouls * 16;
+    size_t sizes[4] = {pg, pg, bg, bg};
+    for (int i = 0; i < 4; ++i)
+      if (outs[i] && sizes[i]) {
+        cudaError_t e = cudaMemsetAsync(outs[i], 0, sizes[i], s);
+        if (e != cudaSuccess) return cuda_fail(e, "zeroing gradients");
+      }
+    g_last_error.clear();
+    return GPP_OK;
+  }
+  gpp::BwdPlan plan;
+  if ((rc = make_bwd_plan(p, o, &plan))) return rc;
+  if (!workspace || !aligned(workspace, gpp::kAlign) || workspace_bytes < plan.total)
+    return fail(GPP_ERR_WORKSPACE, "adjoint workspace must be 256-byte aligned with %zu bytes",
+                plan.total);
+  char* ws = static_cast<char*>(workspace);
+  cudaError_t e = gpp::launch_prep(p, plan.fwd, ws, false, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  if (o.debug_checks) {
+    int flags[4];
+    e = cudaMemcpyAsync(flags, ws + plan.fwd.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
+    if (flags[1] > 0)
+      return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
+                  flags[1]);
+  }
+  e = gpp::launch_bwd(p, o.occ_mode, plan, ws, grad_achtemp, grad_asxtemp, *grads, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernels");
   g_last_error.clear();
   return GPP_OK;
 }

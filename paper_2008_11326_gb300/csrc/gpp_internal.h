@@ -44,6 +44,26 @@ cudaError_t launch_fwd_f64(const gpp_problem& p, int occ_mode, const FwdPlan& pl
 // Main sum with FP32 bulk arithmetic (writes per-CTA partials in FP64).
 cudaError_t launch_fwd_f32(const gpp_problem& p, int occ_mode, const FwdPlan& plan, char* ws,
                            cudaStream_t s);
+// Workspace of the adjoint: the forward's gather segments plus the batch partials.
+struct BwdPlan {
+  FwdPlan fwd;             // flags, colvalid, band table, gathered weights
+  int batch_groups = 1;    // column groups (8 columns each) per main-kernel launch
+  int max_grid = 1;        // persistent grid of the main kernel
+  size_t off_bwd_bt = 0;   // BwdBand[B][W]
+  size_t off_part_n = 0;   // c128[batch_groups][B][G]
+  size_t off_part_r = 0;   // c128[ceil(G/32)][B][batch_groups * 8]
+  size_t off_rtot = 0;     // c128[B][P]
+  size_t total = 0;
+};
+
+int bwd_blocks_per_sm(int nw);
+int64_t bwd_groups(int64_t P);
+int bwd_tile_ig();
+int bwd_tile_cols();
+cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, char* ws,
+                       const gpp_c128* g_ach, const gpp_c128* g_asx, const gpp_grads& out,
+                       cudaStream_t s);
+
 // Fixed-order reduction of the partials into achtemp / asxtemp.
 cudaError_t launch_reduce_final(const FwdPlan& plan, char* ws, gpp_c128* ach, gpp_c128* asx,
                                 cudaStream_t s);

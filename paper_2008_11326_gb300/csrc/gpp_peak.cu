@@ -18,7 +18,47 @@ __device__ __forceinline__ double step(double a, double b, double c) {
   if (KIND == GPP_PEAK_DADD) return a + c;
   if (KIND == GPP_PEAK_DMUL) return a * b;
   if (KIND == GPP_PEAK_DRCP) return gpp::rcp_refined(a);
+  if (KIND == GPP_PEAK_DRCP_APPROX) return gpp::rcp_approx(a);
+  if (KIND == GPP_PEAK_F2F) return static_cast<double>(static_cast<float>(a)) + 0.0;
   return __drcp_rn(a);
+}
+
+// FP32 / integer select and compare chains (for locating which pipe executes them).
+template <int KIND>
+__global__ void peak_sel_kernel(int64_t iters, double* sink) {
+  float v[kChains];
+  int u[kChains];
+  const float lim = 0.5f + 1e-3f * (threadIdx.x & 15);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) {
+    v[k] = 0.25f + 0.07f * k + 1e-4f * threadIdx.x;
+    u[k] = static_cast<int>(threadIdx.x * 7 + k);
+  }
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+      if (KIND == GPP_PEAK_FSEL) {
+        // select between two values derived from v without arithmetic on the FMA pipe
+        const bool c = (u[k] & 1) != 0;
+        v[k] = c ? lim : v[k];
+        u[k] = u[k] ^ 0x5bd1e995;
+      } else if (KIND == GPP_PEAK_FSETP) {
+        u[k] = (v[k] > lim) ? u[k] + 1 : u[k] - 1;
+        v[k] = __int_as_float(__float_as_int(v[k]) ^ (u[k] & 1));
+      } else {
+        const bool c = (u[k] & 2) != 0;
+        u[k] = c ? (u[k] ^ 0x27d4eb2d) : (u[k] + 0x165667b1);
+      }
+    }
+  }
+  float s = 0.0f;
+  int t = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) {
+    s += v[k];
+    t ^= u[k];
+  }
+  if (s == 123.456789f || t == 0x7ffffff3) *sink = s + t;
 }
 
 template <int KIND>
@@ -76,6 +116,11 @@ extern "C" int gpp_peak_launch(int kind, int64_t iters, int blocks, int threads,
     case GPP_PEAK_DMUL: peak_f64_kernel<GPP_PEAK_DMUL><<<blocks, threads, 0, s>>>(iters, sink); break;
     case GPP_PEAK_DRCP: peak_f64_kernel<GPP_PEAK_DRCP><<<blocks, threads, 0, s>>>(iters, sink); break;
     case GPP_PEAK_DRCP_RN: peak_f64_kernel<GPP_PEAK_DRCP_RN><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_DRCP_APPROX: peak_f64_kernel<GPP_PEAK_DRCP_APPROX><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_F2F: peak_f64_kernel<GPP_PEAK_F2F><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_FSEL: peak_sel_kernel<GPP_PEAK_FSEL><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_FSETP: peak_sel_kernel<GPP_PEAK_FSETP><<<blocks, threads, 0, s>>>(iters, sink); break;
+    case GPP_PEAK_ISEL: peak_sel_kernel<GPP_PEAK_ISEL><<<blocks, threads, 0, s>>>(iters, sink); break;
     default: return GPP_ERR_BAD_OPTION;
   }
   return cudaGetLastError() == cudaSuccess ? GPP_OK : GPP_ERR_CUDA;

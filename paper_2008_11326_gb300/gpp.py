@@ -137,6 +137,91 @@ def sigma(dp: DeviceProblem, *, out=None, workspace: torch.Tensor | None = None,
     return ach, asx
 
 
+GRAD_NAMES = ("wtilde", "I_eps", "aqsm", "aqsn")
+
+
+def sigma_backward(dp: DeviceProblem, grad_achtemp: torch.Tensor, grad_asxtemp: torch.Tensor, *,
+                   want=GRAD_NAMES, workspace: torch.Tensor | None = None,
+                   stream: torch.cuda.Stream | None = None, **opts):
+    """Gradients of a real loss through achtemp / asxtemp (PyTorch's complex convention).
+
+    ``grad_achtemp`` / ``grad_asxtemp``: complex128 [nw] device tensors, dL/dRe + i dL/dIm of
+    the outputs. Returns a dict with the requested complex128 gradients: 'wtilde' and
+    'I_eps' [P][G], 'aqsm' and 'aqsn' [B][G].
+    """
+    dev = dp.device
+    shapes = {"wtilde": (dp.ngpown, dp.ncouls), "I_eps": (dp.ngpown, dp.ncouls),
+              "aqsm": (dp.number_bands, dp.ncouls), "aqsn": (dp.number_bands, dp.ncouls)}
+    out = {k: torch.empty(shapes[k], dtype=torch.complex128, device=dev) for k in want}
+    ga = grad_achtemp.to(device=dev, dtype=torch.complex128).contiguous()
+    gs = grad_asxtemp.to(device=dev, dtype=torch.complex128).contiguous()
+    o = make_options(**opts)
+    prob = dp.struct(None, None)
+    lib = N.lib()
+    need = lib.gpp_sigma_backward_workspace_size(ctypes.byref(prob), ctypes.byref(o))
+    if need == 0 and lib.gpp_last_error():
+        raise N.GppError(-2, lib.gpp_last_error().decode())
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    grads = N.GppGrads(*[(out[k].data_ptr() if k in out else None) for k in GRAD_NAMES])
+    N.check(lib.gpp_sigma_backward(ctypes.byref(prob), ctypes.byref(o),
+                                   ctypes.c_void_p(ga.data_ptr()), ctypes.c_void_p(gs.data_ptr()),
+                                   ctypes.byref(grads), ctypes.c_void_p(workspace.data_ptr()),
+                                   workspace.numel(), _stream_handle(stream, dev)))
+    return out
+
+
+class GppSigma(torch.autograd.Function):
+    """(achtemp, asxtemp) = GPP sum, differentiable in aqsmtemp, aqsntemp, I_eps_array and
+    wtilde_array through libgpp's hand-written FP64 adjoint (terms recomputed in backward).
+
+    apply(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index, indinv,
+          wx_array, nvband=0, occ_mode='all')
+    """
+
+    @staticmethod
+    def forward(ctx, aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index,
+                indinv, wx_array, nvband=0, occ_mode="all"):
+        dp = _problem_from(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index,
+                           indinv, wx_array, nvband)
+        ach, asx = sigma(dp, occ_mode=occ_mode)
+        ctx.save_for_backward(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul,
+                              inv_igp_index, indinv, wx_array)
+        ctx.nvband = nvband
+        ctx.occ_mode = occ_mode
+        return ach, asx
+
+    @staticmethod
+    def backward(ctx, g_ach, g_asx):
+        t = ctx.saved_tensors
+        dp = _problem_from(*t, ctx.nvband)
+        W = dp.nw
+        if g_ach is None:
+            g_ach = torch.zeros(W, dtype=torch.complex128, device=dp.device)
+        if g_asx is None:
+            g_asx = torch.zeros(W, dtype=torch.complex128, device=dp.device)
+        need = ctx.needs_input_grad
+        want = [k for k, n in zip(("aqsm", "aqsn", "I_eps", "wtilde"), need[:4]) if n]
+        if not want:
+            return (None,) * 10
+        g = sigma_backward(dp, g_ach, g_asx, want=want, occ_mode=ctx.occ_mode)
+        return (g.get("aqsm"), g.get("aqsn"), g.get("I_eps"), g.get("wtilde"),
+                None, None, None, None, None, None)
+
+
+def _problem_from(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index, indinv,
+                  wx_array, nvband=0) -> DeviceProblem:
+    B, G = aqsmtemp.shape
+    P = wtilde_array.shape[0]
+    W = wx_array.shape[1]
+    c = lambda x, dt: x.detach().to(dt).contiguous()  # noqa: E731
+    return DeviceProblem(B, int(nvband), G, P, W, c(aqsmtemp, torch.complex128),
+                         c(aqsntemp, torch.complex128), c(I_eps_array, torch.complex128),
+                         c(wtilde_array, torch.complex128), c(vcoul, torch.float64),
+                         c(inv_igp_index, torch.int32), c(indinv, torch.int32),
+                         c(wx_array, torch.float64))
+
+
 def host_workspace_size(hp: DeviceProblem, **opts) -> int:
     o = make_options(**opts)
     prob = hp.struct(None, None)

@@ -61,13 +61,14 @@ def test_decisions_next_to_the_branch_threshold(gpp):
 
 def test_next_to_the_wdiff_pole(gpp):
     """Real w with frequencies 1e-9 away from Re w: |wdiff|^2 is 0 in FP32 and 1e-18 in
-    FP64. The branch-2 coefficient is taken in FP64 there; the result stays finite."""
+    FP64. The branch-2 coefficient is taken in FP64 there; the result stays finite. (No
+    frequency equals a w exactly: that is the pole itself, where the sum is undefined.)"""
     prob = inputs.make_problem(6, 2, 256, 4, 3, seed=23)
     wt = prob.wtilde_array.copy()
     vals = np.array([0.75, 1.25, 2.0, 2.5])
     wt[:, :64] = np.tile(vals, 16)[None, :] + 0j
     wx = np.array([[0.75 + 1e-9, 1.25 + 1e-9, 5.0], [2.0 + 1e-9, 2.5 - 1e-9, 0.3],
-                   [1.0, 2.0, 3.0], [4.0, 5.0, 6.0], [0.75 + 2e-9, 7.0, 8.0],
+                   [1.0, 2.2, 3.0], [4.0, 5.0, 6.0], [0.75 + 2e-9, 7.0, 8.0],
                    [9.0, 2.5 + 3e-9, 1.25 - 1e-9]])
     prob = prob.replace(wtilde_array=wt, wx_array=wx)
     got = run(gpp, prob)
