@@ -158,6 +158,23 @@ GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_
 GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void *workspace,
                    size_t workspace_bytes, void *stream);
 
+/*
+ * gpp_sigma without a caller-supplied workspace, for callers that cannot allocate device
+ * memory for it: a Fortran or C host code that links this library through its C interface
+ * and keeps no device allocator of its own, or a process whose device memory is owned and
+ * accounted by another runtime. (No counterpart in the paper: it is an interface option.)
+ * The scratch lives in a fixed array of GPP_NOALLOC_SCRATCH_BYTES inside the library,
+ * which every GPU that loads the library holds until the process exits. The call allocates
+ * nothing and frees nothing. Problems whose gpp_sigma_workspace_size() exceeds the array
+ * are rejected with GPP_ERR_WORKSPACE (the benchmark shape B=512, P=1638, G=32768, nw=3
+ * needs about 14 MB). The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture. All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them. Results equal gpp_sigma's. Asynchronous on `stream`.
+ */
+#define GPP_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+GPP_API int gpp_sigma_noalloc(const gpp_problem *prob, const gpp_options *opt, void *stream);
+
 /* Gradients written by gpp_sigma_backward (device pointers; NULL skips that gradient). */
 typedef struct gpp_grads {
     gpp_c128 *wtilde_array; /* [P][G] */

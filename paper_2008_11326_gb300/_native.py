@@ -56,6 +56,8 @@ SIGNATURES = [
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions)]),
     ("gpp_sigma", ctypes.c_int,
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions), _vp, ctypes.c_size_t, _vp]),
+    ("gpp_sigma_noalloc", ctypes.c_int,
+     [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions), _vp]),
     ("gpp_sigma_host_workspace_size", ctypes.c_size_t,
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions)]),
     ("gpp_sigma_host", ctypes.c_int,

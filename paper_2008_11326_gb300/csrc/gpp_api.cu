@@ -200,6 +200,11 @@ int validate(const gpp_problem* prob, const gpp_options* opt, gpp_options* o) {
 
 }  // namespace
 
+namespace gpp {
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+void clear_error() { g_last_error.clear(); }
+}  // namespace gpp
+
 extern "C" {
 
 void gpp_options_default(gpp_options* opt) {

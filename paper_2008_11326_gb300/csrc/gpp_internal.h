@@ -64,6 +64,10 @@ cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, 
                        const gpp_c128* g_ach, const gpp_c128* g_asx, const gpp_grads& out,
                        cudaStream_t s);
 
+// Sets the thread-local message returned by gpp_last_error(); returns `code`.
+int report_error(int code, const char* msg);
+void clear_error();
+
 // Fixed-order reduction of the partials into achtemp / asxtemp.
 cudaError_t launch_reduce_final(const FwdPlan& plan, char* ws, gpp_c128* ach, gpp_c128* asx,
                                 cudaStream_t s);

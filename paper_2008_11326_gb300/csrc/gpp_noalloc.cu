@@ -1,0 +1,52 @@
+// gpp_sigma_noalloc: gpp_sigma with its scratch in a fixed device array of the library,
+// for callers that cannot hand the library a workspace (see include/gpp.h).
+
+#include <cuda_runtime.h>
+
+#include <stdio.h>
+
+#include <mutex>
+
+#include "gpp.h"
+#include "gpp_internal.h"
+
+namespace {
+
+// The scratch. In host code this symbol is only a stand-in for the device array; its device
+// address comes from cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) unsigned char g_scratch[GPP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mutex;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int gpp_sigma_noalloc(const gpp_problem* prob, const gpp_options* opt, void* stream) {
+  const size_t need = gpp_sigma_workspace_size(prob, opt);
+  if (need == 0 && gpp_last_error()[0] != '\0') return GPP_ERR_BAD_SIZE;  // invalid arguments
+  if (need > GPP_NOALLOC_SCRATCH_BYTES) {
+    char msg[200];
+    snprintf(msg, sizeof(msg),
+             "problem needs %zu bytes of scratch; gpp_sigma_noalloc holds %zu (use gpp_sigma)",
+             need, static_cast<size_t>(GPP_NOALLOC_SCRATCH_BYTES));
+    return gpp::report_error(GPP_ERR_WORKSPACE, msg);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return gpp::report_error(GPP_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return gpp::report_error(GPP_ERR_UNSUPPORTED, "device ordinal too large");
+  void* ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_ptr[dev]) {
+      e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_scratch);
+      if (e != cudaSuccess) {
+        g_scratch_ptr[dev] = nullptr;
+        return gpp::report_error(GPP_ERR_CUDA, cudaGetErrorString(e));
+      }
+    }
+    ptr = g_scratch_ptr[dev];
+  }
+  return gpp_sigma(prob, opt, ptr, GPP_NOALLOC_SCRATCH_BYTES, stream);
+}
