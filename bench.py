@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", choices=["gpp", "reference"], default="gpp")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint and batched measurements")
     ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32"], default=None,
                     help="run only a small instance (B=64, P=256, G=32768, nw=3; 0.3 GB of "
                          "(igp, ig) arrays, more than L2) three times, for ncu captures")
@@ -197,6 +199,98 @@ def measure_peaks(torch, gpp, device):
             "fp64_rcp_per_s": out["drcp"], "sms": sms}
 
 
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def measure_adjoint(torch, gpp, inputs, device, reps=3):
+    """Adjoint workload (B=128, P=410, G=8192, nw=3): backward time against forward time."""
+    prob = inputs.config("adjoint")
+    ga, gs = inputs.cotangents(3, prob.nw)
+    dp = gpp.DeviceProblem.from_host(prob, device=device)
+    ga_t = torch.from_numpy(ga).to(device)
+    gs_t = torch.from_numpy(gs).to(device)
+    gpp.sigma(dp)
+    gpp.sigma_backward(dp, ga_t, gs_t)
+    torch.cuda.synchronize(device)
+    fwd, bwd = [], []
+    for _ in range(reps):
+        e = _events(torch, 3)
+        e[0].record()
+        gpp.sigma(dp)
+        e[1].record()
+        gpp.sigma_backward(dp, ga_t, gs_t)
+        e[2].record()
+        e[2].synchronize()
+        fwd.append(e[0].elapsed_time(e[1]))
+        bwd.append(e[1].elapsed_time(e[2]))
+    f, b = min(fwd), min(bwd)
+    return {"workload": "B128_P410_G8192_nw3", "forward_ms": f, "backward_ms": b,
+            "backward_over_forward": b / f, "target_max_ratio": 3.0}
+
+
+def measure_batched(torch, gpp, inputs, device):
+    """64 uneven instances: one graph-replayed persistent launch (autotuned tile shape)
+    against a loop of per-instance gpp_sigma calls, FP64 and FP32-bulk."""
+    from paper_2008_11326_gb300 import autotune
+    shapes = inputs.batched_shapes()
+    dps = [gpp.DeviceProblem(**inputs.make_device_arrays(**s, device=device)) for s in shapes]
+    units = sum(d.number_bands * d.ngpown * d.ncouls for d in dps)
+    flops = sum(inputs.model_flops(d.number_bands, d.ngpown, d.ncouls, d.nw) for d in dps)
+    out = {"workload": "64 instances, G log-uniform in [2048, 32768], P = G/20, B ~ U{64..512}, "
+                       "nw=3 (inputs drawn on the device)",
+           "units": units, "model_flop": flops}
+    for precision, reps in (("fp64", 1), ("fp32_bulk", 3)):
+        if precision == "fp32_bulk":
+            for d in dps:
+                d.make_c64()
+        tuned = autotune.tune_batched(dps, precision=precision, proxy_bands=8, reps=1)
+        plan = gpp.BatchedPlan(dps, use_graph=True, precision=precision,
+                               block_threads=tuned["block_threads"],
+                               ig_per_thread=tuned["ig_per_thread"])
+        if reps > 1:
+            plan.run()
+        torch.cuda.synchronize(device)
+        g_ms = []
+        for _ in range(reps):
+            e = _events(torch, 2)
+            e[0].record()
+            plan.run()
+            e[1].record()
+            e[1].synchronize()
+            g_ms.append(e[0].elapsed_time(e[1]))
+        batched_res = [torch.cat(o).cpu() for o in plan.outputs]
+        plan.close()
+        wss = [torch.empty(gpp.workspace_size(d, precision=precision), dtype=torch.uint8,
+                           device=device) for d in dps]
+        if reps > 1:
+            for d, w in zip(dps, wss):
+                gpp.sigma(d, workspace=w, precision=precision)
+        torch.cuda.synchronize(device)
+        l_ms = []
+        loop_res = None
+        for _ in range(reps):
+            e = _events(torch, 2)
+            e[0].record()
+            res = [gpp.sigma(d, workspace=w, precision=precision) for d, w in zip(dps, wss)]
+            e[1].record()
+            e[1].synchronize()
+            l_ms.append(e[0].elapsed_time(e[1]))
+            loop_res = [torch.cat(r).cpu() for r in res]
+        del wss
+        diff = max(float(((a - b).abs() / b.abs()).max()) for a, b in zip(batched_res, loop_res))
+        out[precision] = {"graph_ms": min(g_ms), "loop_ms": min(l_ms),
+                          "speedup_vs_loop": min(l_ms) / min(g_ms),
+                          "tflops_model_graph": flops / (min(g_ms) * 1e-3) / 1e12,
+                          "tile": {"block_threads": tuned["block_threads"],
+                                   "ig_per_thread": tuned["ig_per_thread"],
+                                   "from_cache": tuned["cached"]},
+                          "max_rel_diff_vs_loop": diff}
+    del dps
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -317,6 +411,11 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - s0) / e2e_steps
     e2e_ok = bool(np.array_equal(hout[0].numpy(), ref_a) and np.array_equal(hout[1].numpy(), ref_s))
 
+    del hws, hp
+    torch.cuda.empty_cache()
+    adjoint = None if args.no_extras else measure_adjoint(torch, gpp, inputs, device)
+    batched = None if args.no_extras else measure_batched(torch, gpp, inputs, device)
+
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
@@ -355,7 +454,9 @@ def run_gpu(args):
             "gpu_launches": 3 * K,
             "deterministic_across_steps": deterministic,
             "clocks": clk.summary(),
-            "fp32_bulk": fp32_bulk}
+            "fp32_bulk": fp32_bulk,
+            "adjoint": adjoint,
+            "batched": batched}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

@@ -115,7 +115,8 @@ typedef struct gpp_options {
     int32_t block_threads; /* threads per CTA of the main kernel: 0 = default (128), else a multiple of 32 in [64, 256] */
     int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = default */
     int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
-    int32_t reserved[3];   /* must be 0 */
+    int32_t ig_per_thread; /* batched calls: G-vectors each thread takes per tile, 0 = default (1), max 8 */
+    int32_t reserved[2];   /* must be 0 */
     /* NULL, or an array of 4 cudaEvent_t (passed as void*) that the call records on its
      * stream: [0] before the column gather, [1] before the main sum, [2] after it, [3] after
      * the final reduction. For timing the main kernel; the events belong to the caller. */
@@ -201,6 +202,37 @@ GPP_API int gpp_sigma_backward(const gpp_problem *prob, const gpp_options *opt,
                                const gpp_c128 *grad_achtemp, const gpp_c128 *grad_asxtemp,
                                const gpp_grads *grads, void *workspace, size_t workspace_bytes,
                                void *stream);
+
+/*
+ * Batched sums: n independent instances (uneven sizes allowed, the same nw) in one
+ * persistent kernel (an extension of the paper's single-instance kernel). Tiles (one igp
+ * column x block_threads * ig_per_thread G-vectors x all bands) of all instances are taken
+ * from an atomic counter by a grid of blocks_per_sm CTAs per SM, largest band count first;
+ * each tile writes its own partial and a per-instance kernel sums them in a fixed order,
+ * so results are deterministic and equal to gpp_sigma's up to summation order.
+ * `probs` is a host array of n problems with device pointers (each with its own outputs).
+ * The caller provides one device workspace of gpp_batched_workspace_size() bytes.
+ */
+typedef struct gpp_batched_plan gpp_batched_plan; /* opaque host object */
+
+GPP_API size_t gpp_batched_workspace_size(const gpp_problem *probs, int n, const gpp_options *opt);
+
+/*
+ * Prepares a batch: validates every instance, writes the instance descriptors into the
+ * workspace (the call synchronises `stream` once for that), and, with use_graph = 1,
+ * captures gather + persistent kernel + reduction into a CUDA graph on `stream`. The
+ * problems' device arrays and the workspace must stay valid until the plan is destroyed.
+ */
+GPP_API int gpp_batched_plan_create(gpp_batched_plan **plan, const gpp_problem *probs, int n,
+                                    const gpp_options *opt, void *workspace,
+                                    size_t workspace_bytes, int use_graph, void *stream);
+/* Runs a prepared batch on `stream` (a graph launch if the plan holds a graph). */
+GPP_API int gpp_batched_plan_run(gpp_batched_plan *plan, void *stream);
+/* Frees the host-side plan and its graph. */
+GPP_API int gpp_batched_plan_destroy(gpp_batched_plan *plan);
+/* One-shot: create (no graph), run, destroy. */
+GPP_API int gpp_sigma_batched(const gpp_problem *probs, int n, const gpp_options *opt,
+                              void *workspace, size_t workspace_bytes, void *stream);
 
 /* Thread-local description of the last error on this host thread ("" if none). */
 GPP_API const char *gpp_last_error(void);

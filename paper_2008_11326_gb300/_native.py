@@ -45,8 +45,8 @@ class GppGrads(ctypes.Structure):
 
 class GppOptions(ctypes.Structure):
     _fields_ = [("precision", _i32), ("occ_mode", _i32), ("block_threads", _i32),
-                ("blocks_per_sm", _i32), ("debug_checks", _i32), ("reserved", _i32 * 3),
-                ("stage_events", ctypes.POINTER(_vp))]
+                ("blocks_per_sm", _i32), ("debug_checks", _i32), ("ig_per_thread", _i32),
+                ("reserved", _i32 * 2), ("stage_events", ctypes.POINTER(_vp))]
 
 
 # (name, restype, argtypes) of every exported function, in header order.
@@ -67,6 +67,16 @@ SIGNATURES = [
     ("gpp_sigma_backward", ctypes.c_int,
      [ctypes.POINTER(GppProblem), ctypes.POINTER(GppOptions), _vp, _vp,
       ctypes.POINTER(GppGrads), _vp, ctypes.c_size_t, _vp]),
+    ("gpp_batched_workspace_size", ctypes.c_size_t,
+     [ctypes.POINTER(GppProblem), ctypes.c_int, ctypes.POINTER(GppOptions)]),
+    ("gpp_batched_plan_create", ctypes.c_int,
+     [ctypes.POINTER(_vp), ctypes.POINTER(GppProblem), ctypes.c_int, ctypes.POINTER(GppOptions),
+      _vp, ctypes.c_size_t, ctypes.c_int, _vp]),
+    ("gpp_batched_plan_run", ctypes.c_int, [_vp, _vp]),
+    ("gpp_batched_plan_destroy", ctypes.c_int, [_vp]),
+    ("gpp_sigma_batched", ctypes.c_int,
+     [ctypes.POINTER(GppProblem), ctypes.c_int, ctypes.POINTER(GppOptions), _vp,
+      ctypes.c_size_t, _vp]),
     ("gpp_last_error", ctypes.c_char_p, []),
     ("gpp_version", ctypes.c_char_p, []),
     ("gpp_peak_launch", ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
@@ -108,7 +118,7 @@ def check(rc: int):
 
 
 def options(precision=GPP_FP64, occ_mode=GPP_OCC_ALL, block_threads=0, blocks_per_sm=0,
-            debug_checks=False, stage_events=None) -> GppOptions:
+            debug_checks=False, stage_events=None, ig_per_thread=0) -> GppOptions:
     o = GppOptions()
     lib().gpp_options_default(ctypes.byref(o))
     o.precision = precision
@@ -116,6 +126,7 @@ def options(precision=GPP_FP64, occ_mode=GPP_OCC_ALL, block_threads=0, blocks_pe
     o.block_threads = block_threads
     o.blocks_per_sm = blocks_per_sm
     o.debug_checks = 1 if debug_checks else 0
+    o.ig_per_thread = ig_per_thread
     if stage_events is not None:
         arr = (_vp * 4)(*[ctypes.c_void_p(h) for h in stage_events])
         o._events_keepalive = arr

@@ -6,7 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <numeric>
 #include <string>
+#include <vector>
 
 #include "gpp.h"
 #include "gpp_internal.h"
@@ -56,7 +59,9 @@ int check_options(const gpp_options& o) {
     return fail(GPP_ERR_BAD_OPTION, "blocks_per_sm %d must be in [0, 64]", o.blocks_per_sm);
   if (o.debug_checks != 0 && o.debug_checks != 1)
     return fail(GPP_ERR_BAD_OPTION, "debug_checks must be 0 or 1");
-  for (int i = 0; i < 3; ++i)
+  if (o.ig_per_thread < 0 || o.ig_per_thread > 8)
+    return fail(GPP_ERR_BAD_OPTION, "ig_per_thread %d must be in [0, 8]", o.ig_per_thread);
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(GPP_ERR_BAD_OPTION, "reserved option fields must be 0");
   return GPP_OK;
 }
@@ -342,6 +347,208 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernels");
   g_last_error.clear();
   return GPP_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched instances
+
+struct gpp_batched_plan {
+  int n = 0, nw = 0, threads = 128, igpt = 1, grid = 1;
+  bool f32 = false;
+  int64_t ntiles = 0;
+  char* ws = nullptr;
+  size_t total = 0, off_inst = 0, off_counter = 0, off_partials = 0;
+  std::vector<gpp_problem> probs;
+  std::vector<gpp::FwdPlan> iplan;
+  std::vector<size_t> ioff;
+  std::vector<gpp::BatchInst> inst;  // in tile order
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool check_ptrs,
+                   gpp_batched_plan* bp) {
+  if (!probs || n < 1) return fail(GPP_ERR_BAD_SIZE, "batched call needs n >= 1 problems");
+  gpp_options o;
+  int rc = validate(&probs[0], opt, &o);
+  if (rc) return rc;
+  bp->n = n;
+  bp->nw = static_cast<int>(probs[0].nw);
+  bp->f32 = o.precision == GPP_FP32_BULK;
+  if (bp->f32 && !gpp::fwd_f32_available())
+    return fail(GPP_ERR_UNSUPPORTED, "GPP_FP32_BULK is not built into this library");
+  bp->threads = o.block_threads ? o.block_threads : 128;
+  bp->igpt = o.ig_per_thread ? o.ig_per_thread : 1;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+  int bps = o.blocks_per_sm ? o.blocks_per_sm : gpp::batched_blocks_per_sm(bp->threads, bp->nw, bp->f32);
+  if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for the batched kernel");
+  bp->grid = sms * bps;
+  bp->probs.assign(probs, probs + n);
+  bp->iplan.resize(n);
+  bp->ioff.resize(n);
+  size_t off = 0;
+  gpp_options io = o;
+  io.blocks_per_sm = 1;
+  for (int i = 0; i < n; ++i) {
+    const gpp_problem& p = probs[i];
+    if ((rc = check_sizes(p))) return rc;
+    if (p.nw != bp->nw) return fail(GPP_ERR_BAD_SIZE, "instance %d has nw %lld, instance 0 has %d", i, (long long)p.nw, bp->nw);
+    if (degenerate(p)) return fail(GPP_ERR_BAD_SIZE, "instance %d is empty (batched instances need B, P, G >= 1)", i);
+    if (check_ptrs && (rc = check_pointers(p, o.precision))) return rc;
+    if ((rc = make_plan(p, io, &bp->iplan[i]))) return rc;
+    bp->ioff[i] = off;
+    off = gpp::align_up(off + bp->iplan[i].total);
+  }
+  // tile order: instances by band count, largest first (stable)
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return probs[a].number_bands > probs[b].number_bands; });
+  const int64_t per_tile_ig = static_cast<int64_t>(bp->threads) * bp->igpt;
+  bp->inst.assign(n, gpp::BatchInst());
+  int64_t t0 = 0;
+  for (int k = 0; k < n; ++k) {
+    const int i = order[k];
+    const gpp_problem& p = probs[i];
+    gpp::BatchInst& d = bp->inst[k];
+    d.index = i;
+    d.B = static_cast<int>(p.number_bands);
+    d.nocc = static_cast<int>(o.occ_mode == GPP_OCC_OCCUPIED ? std::min(p.nvband, p.number_bands)
+                                                             : p.number_bands);
+    d.G = p.ncouls;
+    d.P = p.ngpown;
+    d.n_ig_tiles = (p.ncouls + per_tile_ig - 1) / per_tile_ig;
+    d.tile0 = t0;
+    t0 += d.P * d.n_ig_tiles;
+    d.tile_end = t0;
+  }
+  bp->ntiles = t0;
+  bp->off_inst = off;
+  off = gpp::align_up(off + static_cast<size_t>(n) * sizeof(gpp::BatchInst));
+  bp->off_counter = off;
+  off = gpp::align_up(off + sizeof(unsigned long long));
+  bp->off_partials = off;
+  off = gpp::align_up(off + static_cast<size_t>(bp->ntiles) * 4 * bp->nw * sizeof(double));
+  bp->total = off;
+  return GPP_OK;
+}
+
+int batched_bind(gpp_batched_plan* bp, void* workspace, size_t bytes) {
+  if (!workspace || !aligned(workspace, gpp::kAlign) || bytes < bp->total)
+    return fail(GPP_ERR_WORKSPACE, "batched workspace must be 256-byte aligned with %zu bytes",
+                bp->total);
+  bp->ws = static_cast<char*>(workspace);
+  for (int k = 0; k < bp->n; ++k) {
+    gpp::BatchInst& d = bp->inst[k];
+    const int i = d.index;
+    const gpp_problem& p = bp->probs[i];
+    const gpp::FwdPlan& pl = bp->iplan[i];
+    char* w = bp->ws + bp->ioff[i];
+    d.aqsn = reinterpret_cast<const double2*>(p.aqsntemp);
+    d.aqsn32 = reinterpret_cast<const float2*>(p.aqsntemp_c64);
+    d.eps = reinterpret_cast<const double2*>(p.I_eps_array);
+    d.wt = reinterpret_cast<const double2*>(p.wtilde_array);
+    d.am = reinterpret_cast<const double2*>(w + pl.off_am);
+    d.am32 = bp->f32 ? reinterpret_cast<const float2*>(w + pl.off_am32) : nullptr;
+    d.bt = reinterpret_cast<const gpp::BandEntry*>(w + pl.off_bt);
+    d.bt32 = bp->f32 ? reinterpret_cast<const gpp::BandEntry32*>(w + pl.off_bt32) : nullptr;
+    d.colg = reinterpret_cast<const int*>(w + pl.off_colvalid);
+    d.flags = reinterpret_cast<const int*>(w + pl.off_flags);
+    d.ach = p.achtemp;
+    d.asx = p.asxtemp;
+  }
+  return GPP_OK;
+}
+
+cudaError_t batched_enqueue(gpp_batched_plan* bp, cudaStream_t s) {
+  for (int i = 0; i < bp->n; ++i) {
+    cudaError_t e = gpp::launch_prep(bp->probs[i], bp->iplan[i], bp->ws + bp->ioff[i], bp->f32, s);
+    if (e != cudaSuccess) return e;
+  }
+  return gpp::launch_batched(reinterpret_cast<const gpp::BatchInst*>(bp->ws + bp->off_inst), bp->n,
+                             bp->ntiles, bp->nw, bp->f32, bp->grid, bp->threads, bp->igpt,
+                             reinterpret_cast<unsigned long long*>(bp->ws + bp->off_counter),
+                             reinterpret_cast<double*>(bp->ws + bp->off_partials), s);
+}
+
+}  // namespace
+
+size_t gpp_batched_workspace_size(const gpp_problem* probs, int n, const gpp_options* opt) {
+  gpp_batched_plan bp;
+  if (batched_layout(probs, n, opt, false, &bp)) return 0;
+  g_last_error.clear();
+  return bp.total;
+}
+
+int gpp_batched_plan_create(gpp_batched_plan** plan, const gpp_problem* probs, int n,
+                            const gpp_options* opt, void* workspace, size_t workspace_bytes,
+                            int use_graph, void* stream) {
+  if (!plan) return fail(GPP_ERR_NULL_PTR, "plan is NULL");
+  *plan = nullptr;
+  gpp_batched_plan* bp = new gpp_batched_plan();
+  int rc = batched_layout(probs, n, opt, true, bp);
+  if (!rc) rc = batched_bind(bp, workspace, workspace_bytes);
+  if (rc) {
+    delete bp;
+    return rc;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(bp->ws + bp->off_inst, bp->inst.data(),
+                                  bp->inst.size() * sizeof(gpp::BatchInst), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete bp;
+    return cuda_fail(e, "uploading the instance descriptors");
+  }
+  if (use_graph) {
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = batched_enqueue(bp, s);
+      e = cudaStreamEndCapture(s, &bp->graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
+    if (e != cudaSuccess) {
+      if (bp->graph) cudaGraphDestroy(bp->graph);
+      delete bp;
+      return cuda_fail(e, "capturing the batched graph");
+    }
+  }
+  *plan = bp;
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+int gpp_batched_plan_run(gpp_batched_plan* plan, void* stream) {
+  if (!plan) return fail(GPP_ERR_NULL_PTR, "plan is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = plan->exec ? cudaGraphLaunch(plan->exec, s) : batched_enqueue(plan, s);
+  if (e != cudaSuccess) return cuda_fail(e, "running the batch");
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+int gpp_batched_plan_destroy(gpp_batched_plan* plan) {
+  if (!plan) return GPP_OK;
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  delete plan;
+  return GPP_OK;
+}
+
+int gpp_sigma_batched(const gpp_problem* probs, int n, const gpp_options* opt, void* workspace,
+                      size_t workspace_bytes, void* stream) {
+  gpp_batched_plan* plan = nullptr;
+  int rc = gpp_batched_plan_create(&plan, probs, n, opt, workspace, workspace_bytes, 0, stream);
+  if (rc) return rc;
+  rc = gpp_batched_plan_run(plan, stream);
+  gpp_batched_plan_destroy(plan);
+  return rc;
 }
 
 // ---------------------------------------------------------------------------------------

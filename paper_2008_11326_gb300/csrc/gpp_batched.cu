@@ -1,0 +1,170 @@
+// Batched GPP sums: many instances of uneven size in one persistent launch.
+//
+// Work unit: a tile = one local column p of one instance x (threads * ig_per_thread)
+// G-vectors, all bands. Tiles of all instances form one list, ordered by instance band count
+// (largest first, so the longest tiles start first and the tail is short). CTAs of a
+// persistent grid take tiles from an atomic counter; the counter only schedules, and every
+// tile writes its own partial slot, so the result does not depend on which CTA ran which
+// tile. A per-instance kernel then sums the instance's tile partials in tile order. The
+// per-tile arithmetic is the single-instance kernels' (gpp_terms_f64.cuh / gpp_terms_f32.cuh).
+
+#include <cuda_runtime.h>
+
+#include "gpp_device.cuh"
+#include "gpp_internal.h"
+#include "gpp_terms_f32.cuh"
+#include "gpp_terms_f64.cuh"
+
+namespace gpp {
+
+namespace {
+
+template <int W, bool F32>
+__global__ void __launch_bounds__(256) gpp_batched_kernel(const BatchInst* __restrict__ inst,
+                                                          int ninst, int64_t ntiles, int igpt,
+                                                          unsigned long long* counter,
+                                                          double* __restrict__ partials) {
+  __shared__ double red[(256 / 32) * 4 * kMaxNw];
+  __shared__ long long s_t;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = static_cast<long long>(atomicAdd(counter, 1ULL));
+    __syncthreads();
+    const int64_t t = s_t;
+    __syncthreads();
+    if (t >= ntiles) break;
+    int lo = 0, hi = ninst - 1;  // instance holding tile t (tile ranges are sorted)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(&inst[mid].tile_end) > t)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    const BatchInst& d = inst[lo];
+    const int B = d.B, nocc = d.nocc;
+    const int64_t G = d.G;
+    const int64_t local = t - d.tile0;
+    const int64_t p = local / d.n_ig_tiles;
+    const int64_t igt = local - p * d.n_ig_tiles;
+    const bool col_ok = d.colg[p] >= 0;
+    const bool x_fast = d.flags[0] == 0 && (!F32 || d.flags[2] == 0);
+    double acc[4 * W];
+#pragma unroll
+    for (int k = 0; k < 4 * W; ++k) acc[k] = 0.0;
+    for (int j = 0; j < igpt; ++j) {
+      const int64_t ig = (igt * igpt + j) * blockDim.x + threadIdx.x;
+      const bool live = ig < G && col_ok;
+      double2 w = make_double2(0.5, 1.0);  // inert lane: finite terms, zero weight
+      double2 I = make_double2(0.0, 0.0);
+      if (live) {
+        w = ldg2(d.wt + p * G + ig);
+        I = ldg2(d.eps + p * G + ig);
+      }
+      const double wabs2 = fma(w.x, w.x, w.y * w.y);
+      const bool fast_lane = w.x >= 0.0 && gt_nonneg(wabs2, kFastWabs2Lo) &&
+                             lt_nonneg(wabs2, kFastWabs2Hi);
+      const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
+      if (F32 && fast) {
+        band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
+                         w, I, acc);
+      } else {
+        const double Iwr = fma(I.x, w.x, -I.y * w.y);
+        const double Iwi = fma(I.x, w.y, I.y * w.x);
+        if (fast)
+          band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                             w.x, w.y, Iwr, Iwi, acc);
+        else
+          band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                              w.x, w.y, Iwr, Iwi, acc);
+      }
+    }
+    block_partials<4 * W>(acc, red, partials + t * 4 * W);
+  }
+}
+
+// One CTA per instance: the instance's tile partials summed in tile order, then a tree.
+__global__ void __launch_bounds__(256) gpp_batched_reduce_kernel(const BatchInst* __restrict__ inst,
+                                                                 int nv,
+                                                                 const double* __restrict__ part) {
+  __shared__ double s[256];
+  const BatchInst& d = inst[blockIdx.x];
+  const int64_t n = d.tile_end - d.tile0;
+  for (int k = 0; k < nv; ++k) {
+    double v = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += 256) v += part[(d.tile0 + j) * nv + k];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+      if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const int iw = k / 4, c = k % 4;
+      if (c < 2)
+        reinterpret_cast<double*>(d.ach)[2 * iw + c] = s[0];
+      else
+        reinterpret_cast<double*>(d.asx)[2 * iw + c - 2] = s[0];
+    }
+    __syncthreads();
+  }
+}
+
+template <int W, bool F32>
+const void* batched_fn() {
+  return reinterpret_cast<const void*>(&gpp_batched_kernel<W, F32>);
+}
+
+const void* batched_kernel_ptr(int nw, bool f32) {
+  switch (nw) {
+    case 1: return f32 ? batched_fn<1, true>() : batched_fn<1, false>();
+    case 2: return f32 ? batched_fn<2, true>() : batched_fn<2, false>();
+    case 3: return f32 ? batched_fn<3, true>() : batched_fn<3, false>();
+    case 4: return f32 ? batched_fn<4, true>() : batched_fn<4, false>();
+    case 5: return f32 ? batched_fn<5, true>() : batched_fn<5, false>();
+    case 6: return f32 ? batched_fn<6, true>() : batched_fn<6, false>();
+    case 7: return f32 ? batched_fn<7, true>() : batched_fn<7, false>();
+    case 8: return f32 ? batched_fn<8, true>() : batched_fn<8, false>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int batched_blocks_per_sm(int threads, int nw, bool f32) {
+  const void* fn = batched_kernel_ptr(nw, f32);
+  if (!fn) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_batched(const BatchInst* inst, int ninst, int64_t ntiles, int nw, bool f32,
+                           int grid, int threads, int igpt, unsigned long long* counter,
+                           double* partials, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+#define GPP_BATCHED_LAUNCH(WV)                                                                    \
+  if (f32)                                                                                        \
+    gpp_batched_kernel<WV, true><<<grid, threads, 0, s>>>(inst, ninst, ntiles, igpt, counter,     \
+                                                          partials);                              \
+  else                                                                                            \
+    gpp_batched_kernel<WV, false><<<grid, threads, 0, s>>>(inst, ninst, ntiles, igpt, counter,    \
+                                                           partials)
+  switch (nw) {
+    case 1: GPP_BATCHED_LAUNCH(1); break;
+    case 2: GPP_BATCHED_LAUNCH(2); break;
+    case 3: GPP_BATCHED_LAUNCH(3); break;
+    case 4: GPP_BATCHED_LAUNCH(4); break;
+    case 5: GPP_BATCHED_LAUNCH(5); break;
+    case 6: GPP_BATCHED_LAUNCH(6); break;
+    case 7: GPP_BATCHED_LAUNCH(7); break;
+    case 8: GPP_BATCHED_LAUNCH(8); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef GPP_BATCHED_LAUNCH
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  gpp_batched_reduce_kernel<<<ninst, 256, 0, s>>>(inst, 4 * nw, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace gpp

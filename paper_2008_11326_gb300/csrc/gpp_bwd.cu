@@ -59,6 +59,11 @@ __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 csel(bool c, double2 a, double2 b) { return c ? a : b; }
 
+template <bool V>
+struct BoolTag {
+  static constexpr bool value = V;
+};
+
 __global__ void gpp_bwd_prep_kernel(int64_t B, int W, const double* __restrict__ wx,
                                     const double2* __restrict__ g_ach,
                                     const double2* __restrict__ g_asx, BwdBand* bt) {
@@ -83,8 +88,8 @@ __global__ void gpp_bwd_prep_kernel(int64_t B, int W, const double* __restrict__
 }
 
 // Per-term work for one band, all frequencies: accumulates GI and GW.
-template <int W, bool FAST>
-__device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, bool occ, double wr,
+template <int W, bool FAST, bool OCC>
+__device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double wr,
                                           double wi, double wi2, double wabs2, double mw2r,
                                           double w2i, double2 w, double2& GI, double2& GW) {
 #pragma unroll
@@ -109,7 +114,7 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, bool oc
     const double2 u = make_double2(Ar * a1, wi * a1);          // 1/(x - w) on branch 1
     cmac(GI, __ldg(&e[iw].ca), u);
     cmac(GW, __ldg(&e[iw].cax), cmul(u, u));
-    if (occ) {
+    if (OCC) {
       const double b2 = A2 * r;
       const double2 v = make_double2(Sr * b2, -wi * b2);       // 1/(x + w)
       const double2 uv = make_double2((x2 + mw2r) * r, w2i * r);  // 1/(x^2 - w^2)
@@ -189,15 +194,17 @@ __global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
     const double2* an_ptr = aqsn + (ig < G ? ig : 0);
     const double2* am_ptr = am + (col_ok ? p : 0) * B;
     double2 gw = make_double2(0.0, 0.0), gI = make_double2(0.0, 0.0);
-    for (int b = 0; b < B; ++b) {
+    // bands [0, nocc) enter asxtemp too; OCC is a template parameter of the band body
+    auto band = [&](int b, auto occ_tag) {
+      constexpr bool OCC = decltype(occ_tag)::value;
       const double2 an = (ig < G) ? ldg2(an_ptr + static_cast<int64_t>(b) * G) : make_double2(0.0, 0.0);
       const double2 amv = col_ok ? ldg2(am_ptr + b) : make_double2(0.0, 0.0);
       double2 GI = make_double2(0.0, 0.0), GW = make_double2(0.0, 0.0);
       const BwdBand* e = bt + static_cast<int64_t>(b) * W;
       if (fast)
-        bwd_terms<W, true>(e, b < nocc, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
+        bwd_terms<W, true, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
       else
-        bwd_terms<W, false>(e, b < nocc, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
+        bwd_terms<W, false, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
       const double2 M = cmul(amv, an);
       cmac(gI, cmul(M, w), GI);
       cmac(gw, cmul(M, I), GW);
@@ -211,7 +218,9 @@ __global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
       if (tx == 0)
         part_r[(igt * B + b) * (static_cast<int64_t>(ngroups) * kTY) + gl * kTY + ty] = s_r[ty][0];
       __syncthreads();
-    }
+    };
+    for (int b = 0; b < nocc; ++b) band(b, BoolTag<true>());
+    for (int b = nocc; b < B; ++b) band(b, BoolTag<false>());
     if (live) {
       if (grad_w) grad_w[p * G + ig] = make_double2(gw.x, -gw.y);
       if (grad_I) grad_I[p * G + ig] = make_double2(gI.x, -gI.y);

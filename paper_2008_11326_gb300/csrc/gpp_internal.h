@@ -9,6 +9,9 @@
 
 namespace gpp {
 
+struct BandEntry;
+struct BandEntry32;
+
 // Layout of the caller's workspace for one forward call. Every segment starts on a
 // 256-byte boundary.
 struct FwdPlan {
@@ -63,6 +66,32 @@ int bwd_tile_cols();
 cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, char* ws,
                        const gpp_c128* g_ach, const gpp_c128* g_asx, const gpp_grads& out,
                        cudaStream_t s);
+
+// One instance of a batched launch (device-resident descriptor; see gpp_batched.cu).
+struct BatchInst {
+  int B = 0, nocc = 0;
+  int index = 0;  // position of the instance in the caller's array
+  int pad = 0;
+  int64_t G = 0, P = 0, n_ig_tiles = 0, tile0 = 0, tile_end = 0;
+  const double2* aqsn = nullptr;
+  const float2* aqsn32 = nullptr;
+  const double2* eps = nullptr;
+  const double2* wt = nullptr;
+  const double2* am = nullptr;
+  const float2* am32 = nullptr;
+  const BandEntry* bt = nullptr;
+  const BandEntry32* bt32 = nullptr;
+  const int* colg = nullptr;
+  const int* flags = nullptr;
+  gpp_c128* ach = nullptr;
+  gpp_c128* asx = nullptr;
+};
+
+int batched_blocks_per_sm(int threads, int nw, bool f32);
+// Resets the tile counter, runs the persistent kernel and the per-instance reduction.
+cudaError_t launch_batched(const BatchInst* inst, int ninst, int64_t ntiles, int nw, bool f32,
+                           int grid, int threads, int igpt, unsigned long long* counter,
+                           double* partials, cudaStream_t s);
 
 // Sets the thread-local message returned by gpp_last_error(); returns `code`.
 int report_error(int code, const char* msg);

@@ -1,0 +1,166 @@
+// The FP32-bulk per-band evaluation (shared by the single-instance and batched kernels).
+// The precision choices are described at the top of gpp_fwd_f32.cu.
+#pragma once
+
+#include "gpp_device.cuh"
+
+namespace gpp {
+
+constexpr int kChunk = 32;            // bands summed in plain FP32 before a Kahan merge
+constexpr float kPoleA2 = 9.313225746154785e-10f;  // 2^-30
+
+__device__ __forceinline__ float rcp_approx_f32(float d) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d));
+  return y;
+}
+
+__device__ __forceinline__ float2 ldgf2(const float2* p) { return __ldg(p); }
+
+// Select on the integer pipe. A plain conditional between two floats can be issued as a
+// floating-point select, which GB300 executes on its (narrow) FP64 pipe; the bitwise
+// selp.b32 keeps it on the integer ALU.
+__device__ __forceinline__ float isel(bool c, float a, float b) {
+  float r;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tselp.b32 %0, %1, %2, q;\n\t}"
+      : "=f"(r)
+      : "f"(a), "f"(b), "r"(static_cast<int>(c)));
+  return r;
+}
+
+// Per-(igp, ig) constants of the FP32 path.
+struct PairF32 {
+  float wr, wi, wi2, mw2r, w2i, wrh, wih, Iwr, Iwi, wm;
+  double wr64, wi2_64;
+};
+
+// Bands [b0, b1) into the chunk sums c. OCC (whether these bands enter asxtemp) is a
+// template parameter: a runtime flag in this loop body costs instructions.
+template <int W, bool OCC>
+__device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float2* __restrict__ an_ptr,
+                                          const float2* __restrict__ am_ptr,
+                                          const BandEntry32* __restrict__ bt32,
+                                          const BandEntry* __restrict__ bt64, const PairF32& q,
+                                          float (&c)[4 * W]) {
+#pragma unroll 1
+  for (int b = b0; b < b1; ++b) {
+    // inert lanes read a valid element; their I = 0 makes every product vanish
+    const float2 an = ldgf2(an_ptr + static_cast<int64_t>(b) * G);
+    const float2 am = ldgf2(am_ptr + b);
+    const float Mr = fmaf(am.x, an.x, -am.y * an.y);
+    const float Mi = fmaf(am.x, an.y, am.y * an.x);
+    const float Kr = fmaf(Mr, q.Iwr, -Mi * q.Iwi);
+    const float Ki = fmaf(Mr, q.Iwi, Mi * q.Iwr);
+    const float K2r = fmaf(Kr, q.wr, -Ki * q.wi);
+    const float K2i = fmaf(Kr, q.wi, Ki * q.wr);
+    const float Kwr = -Ki * q.wi, Kwi = Kr * q.wi;
+    const float P1r = -K2i * q.w2i, P1i = K2r * q.w2i;
+    const BandEntry32* e = bt32 + static_cast<int64_t>(b) * W;
+#pragma unroll
+    for (int iw = 0; iw < W; ++iw) {
+      const float4 ea = __ldg(&e[iw].a);
+      const float xm = __ldg(&e[iw].b.x);
+      const float x = ea.x, x2 = ea.y, x4 = ea.z, xh = ea.w;
+      const float Ar = x - q.wr;
+      const float A2 = fmaf(Ar, Ar, q.wi2);
+      const float S2 = fmaf(x4, q.wr, A2);
+      float r = rcp_approx_f32(A2 * S2);
+      float b2 = A2 * r;
+      const float d = A2 - 0.25f;
+      bool c1 = d > 0.0f;
+      const bool near = fabsf(d) <= xm + q.wm;
+      const bool pole = A2 < kPoleA2;
+      if (__any_sync(0xffffffffu, near || pole)) {
+        if (near || pole) {
+          const double x64 = __ldg(&bt64[static_cast<int64_t>(b) * W + iw].lo.x);
+          if (near) {  // decide exactly as the FP64 kernel
+            const double a64 = x64 - q.wr64;
+            c1 = gt_nonneg(fma(a64, a64, q.wi2_64), kLimitTwo);
+          }
+          if (pole) {  // 1/|x + w|^2 in FP64 next to the pole; r only feeds branch 1
+            const double s64 = x64 + q.wr64;
+            b2 = static_cast<float>(rcp_refined(fma(s64, s64, q.wi2_64)));
+            r = 0.0f;
+          }
+        }
+      }
+      const float tr = fmaf(Kr, Ar, Kwr);
+      const float ti = fmaf(Ki, Ar, Kwi);
+      if (__all_sync(0xffffffffu, c1)) {
+        // every lane on branch 1: K conj(A) / |A|^2 and K2 conj(C) / |C|^2
+        const float a1 = S2 * r;
+        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
+        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+        if (OCC) {
+          const float Yr = x2 + q.mw2r;
+          const float ur = fmaf(K2r, Yr, P1r);
+          const float ui = fmaf(K2i, Yr, P1i);
+          c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
+          c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
+        }
+      } else {
+        const float a1 = isel(c1, S2 * r, 0.0f);
+        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
+        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+        if (OCC) {
+          // branch 2: K (-conj(S)/2) / |S|^2 = (Re K Yr - Im K Im w/2, Im K Yr + Re K Im w/2) b2
+          const float coef = isel(c1, r, b2);
+          const float Yr = isel(c1, x2, xh) + isel(c1, q.mw2r, q.wrh);
+          const float ur = fmaf(isel(c1, K2r, Kr), Yr, isel(c1, P1r, -Ki * q.wih));
+          const float ui = fmaf(isel(c1, K2i, Ki), Yr, isel(c1, P1i, Kr * q.wih));
+          c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
+          c[4 * iw + 3] = fmaf(ui, coef, c[4 * iw + 3]);
+        }
+      }
+    }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
+                                              const float2* __restrict__ an_ptr,
+                                              const float2* __restrict__ am_ptr,
+                                              const BandEntry32* __restrict__ bt32,
+                                              const BandEntry* __restrict__ bt64,
+                                              double2 w64, double2 I64, double (&acc)[4 * W]) {
+  PairF32 q;
+  q.wr = static_cast<float>(w64.x);
+  q.wi = static_cast<float>(w64.y);
+  const float Ir = static_cast<float>(I64.x), Ii = static_cast<float>(I64.y);
+  q.wi2 = q.wi * q.wi;
+  q.mw2r = -fmaf(q.wr, q.wr, -q.wi2);   // -Re w^2
+  q.w2i = 2.0f * q.wr * q.wi;           // Im w^2
+  q.wrh = -0.5f * q.wr;
+  q.wih = 0.5f * q.wi;
+  q.Iwr = fmaf(Ir, q.wr, -Ii * q.wi);
+  q.Iwi = fmaf(Ir, q.wi, Ii * q.wr);
+  q.wm = kMarginScale * fabsf(q.wr);
+  q.wr64 = w64.x;
+  q.wi2_64 = w64.y * w64.y;
+  float hi[4 * W], lo[4 * W];
+#pragma unroll
+  for (int k = 0; k < 4 * W; ++k) hi[k] = lo[k] = 0.0f;
+#pragma unroll 1
+  for (int b0 = 0; b0 < B; b0 += kChunk) {
+    float c[4 * W];
+#pragma unroll
+    for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
+    const int bend = min(b0 + kChunk, B);
+    const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
+    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, bt64, q, c);
+    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, bt64, q, c);
+    // Kahan merge of the chunk sums: hi + lo carries the running sum, lo the lost low part
+#pragma unroll
+    for (int k = 0; k < 4 * W; ++k) {
+      const float y = c[k] - lo[k];
+      const float t = hi[k] + y;
+      lo[k] = (t - hi[k]) - y;
+      hi[k] = t;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4 * W; ++k)
+    acc[k] += static_cast<double>(hi[k]) - static_cast<double>(lo[k]);
+}
+
+}  // namespace gpp

@@ -22,8 +22,8 @@ struct BandK {
   double Kr, Ki, K2r, K2i, Kwr, Kwi, P1r, P1i, P2r, P2i;
 };
 
-template <int W, bool FAST>
-__device__ __forceinline__ void band_terms(const BandK& k, bool occ,
+template <int W, bool FAST, bool OCC>
+__device__ __forceinline__ void band_terms(const BandK& k,
                                            const BandEntry* __restrict__ btb, double wr,
                                            double wi2, double wabs2, double mw2r, double wrh,
                                            double (&acc)[4 * W]) {
@@ -54,7 +54,7 @@ __device__ __forceinline__ void band_terms(const BandK& k, bool occ,
     const double ti = fma(k.Ki, Ar, k.Kwi);
     acc[4 * iw + 0] = fma(tr, a1, acc[4 * iw + 0]);
     acc[4 * iw + 1] = fma(ti, a1, acc[4 * iw + 1]);
-    if (occ) {
+    if (OCC) {
       // asxtemp: branch 1 -> K2 conj(C) / |C|^2,  branch 2 -> K (-conj(S)/2) / |S|^2
       const double b2 = A2 * r;
       const double coef = c1 ? r : (c2 ? b2 : 0.0);
@@ -67,23 +67,20 @@ __device__ __forceinline__ void band_terms(const BandK& k, bool occ,
   }
 }
 
-template <int W, bool FAST>
-__device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
-                                          const double2* __restrict__ an_ptr,
-                                          const double2* __restrict__ am_ptr,
-                                          const BandEntry* __restrict__ bt, bool live,
-                                          double wr, double wi, double Iwr, double Iwi,
-                                          double (&acc)[4 * W]) {
-  const double wi2 = wi * wi;
-  const double wabs2 = fma(wr, wr, wi2);
-  const double mw2r = -fma(wr, wr, -wi2);   // -Re w^2
-  const double w2i = 2.0 * wr * wi;         // Im w^2
-  const double wrh = -0.5 * wr;
-  const double wih = 0.5 * wi;
+// Bands [b0, b1) of the thread's (p, ig) pair. OCC says whether these bands enter asxtemp;
+// it is a template parameter because a runtime flag in this loop body costs FP64
+// instructions (the compiler schedules the asxtemp terms around it).
+template <int W, bool FAST, bool OCC>
+__device__ __forceinline__ void band_range(int b0, int b1, int64_t G,
+                                           const double2* __restrict__ an_ptr,
+                                           const double2* __restrict__ am_ptr,
+                                           const BandEntry* __restrict__ bt, bool live, double wr,
+                                           double wi, double Iwr, double Iwi, double wi2,
+                                           double wabs2, double mw2r, double w2i, double wrh,
+                                           double wih, double (&acc)[4 * W]) {
 #pragma unroll 1
-  for (int b = 0; b < B; ++b) {
-    const double2 an = live ? ldg2(an_ptr) : make_double2(0.0, 0.0);
-    an_ptr += G;
+  for (int b = b0; b < b1; ++b) {
+    const double2 an = live ? ldg2(an_ptr + static_cast<int64_t>(b) * G) : make_double2(0.0, 0.0);
     const double2 am = ldg2(am_ptr + b);
     BandK k;
     // M = am * an with am = conj(aqsmtemp[b][g]) vcoul[g]; K = M I w; K2 = K w
@@ -99,9 +96,30 @@ __device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
     k.P1i = k.K2r * w2i;
     k.P2r = -k.Ki * wih;
     k.P2i = k.Kr * wih;
-    band_terms<W, FAST>(k, b < nocc, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r,
-                        wrh, acc);
+    band_terms<W, FAST, OCC>(k, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r, wrh, acc);
   }
+}
+
+// All bands of the thread's (p, ig) pair: bands [0, nocc) enter both sums, the rest only
+// achtemp.
+template <int W, bool FAST>
+__device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
+                                          const double2* __restrict__ an_ptr,
+                                          const double2* __restrict__ am_ptr,
+                                          const BandEntry* __restrict__ bt, bool live,
+                                          double wr, double wi, double Iwr, double Iwi,
+                                          double (&acc)[4 * W]) {
+  const double wi2 = wi * wi;
+  const double wabs2 = fma(wr, wr, wi2);
+  const double mw2r = -fma(wr, wr, -wi2);   // -Re w^2
+  const double w2i = 2.0 * wr * wi;         // Im w^2
+  const double wrh = -0.5 * wr;
+  const double wih = 0.5 * wi;
+  band_range<W, FAST, true>(0, nocc, G, an_ptr, am_ptr, bt, live, wr, wi, Iwr, Iwi, wi2, wabs2,
+                            mw2r, w2i, wrh, wih, acc);
+  if (nocc < B)
+    band_range<W, FAST, false>(nocc, B, G, an_ptr, am_ptr, bt, live, wr, wi, Iwr, Iwi, wi2, wabs2,
+                               mw2r, w2i, wrh, wih, acc);
 }
 
 }  // namespace gpp

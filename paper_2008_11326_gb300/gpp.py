@@ -91,13 +91,13 @@ def _stream_handle(stream, device):
 
 
 def make_options(precision="fp64", occ_mode="all", block_threads=0, blocks_per_sm=0,
-                 debug_checks=False, stage_events=None) -> N.GppOptions:
+                 debug_checks=False, stage_events=None, ig_per_thread=0) -> N.GppOptions:
     """``stage_events``: four recorded ``torch.cuda.Event(enable_timing=True)`` (or raw
     cudaEvent_t handles) that the call re-records around its stages (see gpp_options)."""
     if stage_events is not None:
         stage_events = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in stage_events]
     return N.options(PRECISIONS[precision], OCC_MODES[occ_mode], block_threads, blocks_per_sm,
-                     debug_checks, stage_events)
+                     debug_checks, stage_events, ig_per_thread)
 
 
 def workspace_size(dp: DeviceProblem, **opts) -> int:
@@ -135,6 +135,49 @@ def sigma(dp: DeviceProblem, *, out=None, workspace: torch.Tensor | None = None,
     N.check(lib.gpp_sigma(ctypes.byref(prob), ctypes.byref(o), ctypes.c_void_p(workspace.data_ptr()),
                           workspace.numel(), _stream_handle(stream, dev)))
     return ach, asx
+
+
+class BatchedPlan:
+    """A prepared batch of instances (one persistent launch, optionally a CUDA graph).
+
+    ``dps``: list of :class:`DeviceProblem` (same nw). Outputs are per-instance complex128
+    [nw] device tensors in ``self.outputs``. ``run()`` enqueues the batch on the current
+    stream (a graph replay when ``use_graph``).
+    """
+
+    def __init__(self, dps, *, use_graph=True, stream=None, **opts):
+        self.dps = list(dps)
+        dev = self.dps[0].device
+        self.outputs = [(torch.empty(d.nw, dtype=torch.complex128, device=dev),
+                         torch.empty(d.nw, dtype=torch.complex128, device=dev)) for d in self.dps]
+        self._structs = (N.GppProblem * len(self.dps))(
+            *[d.struct(a, s) for d, (a, s) in zip(self.dps, self.outputs)])
+        self._opts = make_options(**opts)
+        lib = N.lib()
+        need = lib.gpp_batched_workspace_size(self._structs, len(self.dps), ctypes.byref(self._opts))
+        if need == 0:
+            raise N.GppError(-2, lib.gpp_last_error().decode())
+        self.workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+        self._handle = ctypes.c_void_p()
+        N.check(lib.gpp_batched_plan_create(ctypes.byref(self._handle), self._structs,
+                                            len(self.dps), ctypes.byref(self._opts),
+                                            ctypes.c_void_p(self.workspace.data_ptr()), need,
+                                            1 if use_graph else 0, _stream_handle(stream, dev)))
+
+    def run(self, stream=None):
+        N.check(N.lib().gpp_batched_plan_run(self._handle, _stream_handle(stream, self.workspace.device)))
+        return self.outputs
+
+    def close(self):
+        if self._handle:
+            N.lib().gpp_batched_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 GRAD_NAMES = ("wtilde", "I_eps", "aqsm", "aqsn")

@@ -119,6 +119,39 @@ def make_problem(number_bands: int, nvband: int, ncouls: int, ngpown: int, nw: i
                       inv, indinv, np.ascontiguousarray(wx))
 
 
+def make_device_arrays(number_bands: int, nvband: int, ncouls: int, ngpown: int, nw: int,
+                       seed: int, device, e_lk: float = E_LK, dw: float = DW) -> dict:
+    """The same distributions as :func:`make_problem`, drawn on ``device`` with a seeded
+    ``torch.Generator`` (different values from the numpy draw of the same seed). For
+    workloads too large to draw on the host each run; returns a dict of torch tensors with
+    the field names of :class:`GppProblem`."""
+    import torch
+    B, G, P, W = int(number_bands), int(ncouls), int(ngpown), int(nw)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device)
+
+    def u(shape, lo, hi):
+        return torch.rand(shape, generator=g, **f64) * (hi - lo) + lo
+
+    def c(shape, rl, rh, il, ih):
+        return torch.complex(u(shape, rl, rh), u(shape, il, ih))
+    out = dict(number_bands=B, nvband=int(nvband), ncouls=G, ngpown=P, nw=W)
+    out["aqsmtemp"] = c((B, G), -1.0, 1.0, -1.0, 1.0)
+    out["aqsntemp"] = c((B, G), -1.0, 1.0, -1.0, 1.0)
+    out["I_eps_array"] = c((P, G), 0.5, 1.5, -0.1, 0.1)
+    out["wtilde_array"] = c((P, G), 0.2, 3.0, -0.05, 0.05)
+    out["vcoul"] = u((G,), 0.1, 10.0)
+    out["inv_igp_index"] = torch.randperm(G, generator=g, device=device)[:P].to(torch.int32)
+    ind = torch.empty(G + 1, dtype=torch.int32, device=device)
+    ind[:G] = torch.randperm(G, generator=g, device=device).to(torch.int32)
+    ind[G] = G
+    out["indinv"] = ind
+    e_n1 = u((B,), 0.0, 10.0)
+    out["wx_array"] = ((e_lk - e_n1)[:, None] + dw * torch.arange(W, **f64)[None, :]).contiguous()
+    return out
+
+
 def cotangents(seed: int, nw: int):
     """Loss weights a_iw, b_iw ~ N(0, 1) for L = sum_iw a_iw Re ach[iw] + b_iw Im asx[iw].
 
