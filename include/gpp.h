@@ -220,7 +220,8 @@ GPP_API size_t gpp_batched_workspace_size(const gpp_problem *probs, int n, const
 /*
  * Prepares a batch: validates every instance, writes the instance descriptors into the
  * workspace (the call synchronises `stream` once for that), and, with use_graph = 1,
- * captures gather + persistent kernel + reduction into a CUDA graph on `stream`. The
+ * captures gather + persistent kernel + reduction into a CUDA graph (on a private stream;
+ * runs launch it on the caller's stream). The
  * problems' device arrays and the workspace must stay valid until the plan is destroyed.
  */
 GPP_API int gpp_batched_plan_create(gpp_batched_plan **plan, const gpp_problem *probs, int n,

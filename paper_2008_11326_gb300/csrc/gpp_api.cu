@@ -506,12 +506,17 @@ int gpp_batched_plan_create(gpp_batched_plan** plan, const gpp_problem* probs, i
     return cuda_fail(e, "uploading the instance descriptors");
   }
   if (use_graph) {
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    // Captured on a private stream (the caller's may be the legacy default stream, which
+    // cannot be captured); the graph is later launched on the caller's stream.
+    cudaStream_t cs = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = batched_enqueue(bp, s);
-      e = cudaStreamEndCapture(s, &bp->graph);
+      cudaError_t e2 = batched_enqueue(bp, cs);
+      e = cudaStreamEndCapture(cs, &bp->graph);
       if (e2 != cudaSuccess) e = e2;
     }
+    if (cs) cudaStreamDestroy(cs);
     if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
     if (e != cudaSuccess) {
       if (bp->graph) cudaGraphDestroy(bp->graph);
