@@ -43,9 +43,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint and batched measurements")
-    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32"], default=None,
-                    help="run only a small instance (B=64, P=256, G=32768, nw=3; 0.3 GB of "
-                         "(igp, ig) arrays, more than L2) three times, for ncu captures")
+    ap.add_argument("--pipe-rates", action="store_true",
+                    help="print the throughput of every instruction kind of the library's "
+                         "throughput kernels (machine characterisation) and exit")
+    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32", "bwd", "batched"],
+                    default=None,
+                    help="run only a small case three times, for ncu captures: fwd_* and bwd "
+                         "use B=64, P=256, G=32768, nw=3 (0.3 GB of (igp, ig) arrays, more "
+                         "than L2); batched uses 8 instances with G in [2048, 32768] and B=32")
     return ap.parse_args()
 
 
@@ -173,6 +178,23 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(pw) if pw else None, "samples": len(rows),
                 "reasons": reasons}
+
+
+def recorded_traffic():
+    """DRAM bytes per main-kernel launch from the committed ncu capture, if the kernel's
+    sources are unchanged since (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec["traffic_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
 
 
 def measure_peaks(torch, gpp, device):
@@ -424,8 +446,11 @@ def run_gpu(args):
     main_avg_s = statistics.mean(main_ms) * 1e-3
     achieved = flops / main_avg_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"],
-                "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"], "traffic": None,
-                "kernel": "gpp_fwd_f64_kernel<3>",
+                "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"],
+                "traffic": recorded_traffic(),
+                "algorithmic_bytes": 2.0 * prob.ngpown * prob.ncouls * 16 + prob.number_bands * prob.ncouls * 16
+                + prob.number_bands * prob.ngpown * 16 + prob.ncouls * 8 + prob.number_bands * prob.nw * 8,
+                "kernel": "gpp_batched_kernel<3, false> (main sum of gpp_sigma)",
                 "peak_source": "DFMA-chain throughput kernel measured in this run, all SMs "
                                "(FP64 pipe; FMA = 2 FLOP)",
                 "achieved_source": "model FLOP (159 per band x igp x ig) / mean CUDA-event "
@@ -467,9 +492,26 @@ def run_profile_case(args):
     import torch
 
     from paper_2008_11326_gb300 import gpp, inputs
+    if args.profile_case == "batched":
+        shapes = inputs.batched_shapes(8)
+        dps = [gpp.DeviceProblem(**inputs.make_device_arrays(**dict(s, number_bands=32),
+                                                             device="cuda")) for s in shapes]
+        plan = gpp.BatchedPlan(dps, use_graph=False, block_threads=64, ig_per_thread=4)
+        for _ in range(3):
+            outs = plan.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "batched", "achtemp0": str(outs[0][0][0].item())}))
+        return 0
     prob = inputs.make_problem(64, 2, 32768, 256, 3, seed=1)
     precision = "fp32_bulk" if args.profile_case == "fwd_f32" else "fp64"
     dp = gpp.DeviceProblem.from_host(prob, device="cuda", c64=precision == "fp32_bulk")
+    if args.profile_case == "bwd":
+        ga, gs = inputs.cotangents(3, prob.nw)
+        for _ in range(3):
+            g = gpp.sigma_backward(dp, torch.from_numpy(ga).cuda(), torch.from_numpy(gs).cuda())
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "bwd", "grad0": str(g["wtilde"][0, 0].item())}))
+        return 0
     for _ in range(3):
         ach, asx = gpp.sigma(dp, precision=precision)
     torch.cuda.synchronize()
@@ -477,10 +519,41 @@ def run_profile_case(args):
     return 0
 
 
+def run_pipe_rates():
+    """Throughput of each instruction kind on all SMs (8 independent chains per thread)."""
+    import torch
+
+    from paper_2008_11326_gb300 import gpp
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {}
+    for kind, iters in (("dfma", 256), ("dadd", 256), ("dmul", 256), ("drcp", 128),
+                        ("drcp_approx", 512), ("drcp_rn", 64), ("ffma", 8192),
+                        ("fsetp", 8192), ("isel", 8192)):
+        blocks, threads = sms * 4, 256
+        gpp.peak_launch(kind, max(iters // 8, 1), blocks, threads, sink)
+        torch.cuda.synchronize(dev)
+        best = 0.0
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ops = gpp.peak_launch(kind, iters, blocks, threads, sink)
+            e1.record()
+            e1.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) * 1e-3))
+        out[kind] = {"ops_per_s": best, "per_clk_per_sm_at_2070MHz": best / (sms * 2.07e9)}
+    print(json.dumps({"pipe_rates": out, "sms": sms}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.pipe_rates:
+        return run_pipe_rates()
     if args.profile_case:
         return run_profile_case(args)
     return run_gpu(args)

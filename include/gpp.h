@@ -113,9 +113,10 @@ typedef struct gpp_options {
     int32_t precision;     /* gpp_precision */
     int32_t occ_mode;      /* gpp_occ_mode */
     int32_t block_threads; /* threads per CTA of the main kernel: 0 = default (128), else a multiple of 32 in [64, 256] */
-    int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = default */
+    int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = as many as fit */
     int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
-    int32_t ig_per_thread; /* batched calls: G-vectors each thread takes per tile, 0 = default (1), max 8 */
+    int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4), max 8; a tile is
+                              one igp column x block_threads * ig_per_thread G-vectors x all bands */
     int32_t reserved[2];   /* must be 0 */
     /* NULL, or an array of 4 cudaEvent_t (passed as void*) that the call records on its
      * stream: [0] before the column gather, [1] before the main sum, [2] after it, [3] after
@@ -137,7 +138,8 @@ GPP_API size_t gpp_sigma_workspace_size(const gpp_problem *prob, const gpp_optio
  * The forward sum (achtemp, asxtemp) of one instance. `workspace` is a device buffer of at
  * least gpp_sigma_workspace_size() bytes, 256-byte aligned, owned by the caller and not
  * used concurrently by another call. The call enqueues three kernels on `stream` (column
- * gather, main sum, deterministic final reduction) and returns without synchronising,
+ * gather, main sum over tiles taken from a counter by a persistent grid with one partial
+ * per tile, fixed-order reduction of the partials) and returns without synchronising,
  * except with debug_checks = 1, where it synchronises `stream` to report bad indices.
  * Errors: NULL_PTR, BAD_SIZE, BAD_OPTION, WORKSPACE, CUDA, BAD_INDEX (debug_checks only).
  */
@@ -168,12 +170,12 @@ GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void
  * which every GPU that loads the library holds until the process exits. The call allocates
  * nothing and frees nothing. Problems whose gpp_sigma_workspace_size() exceeds the array
  * are rejected with GPP_ERR_WORKSPACE (the benchmark shape B=512, P=1638, G=32768, nw=3
- * needs about 14 MB). The first call on a device looks up the array's device address with
+ * needs about 24 MB with the default tiles). The first call on a device looks up the array's device address with
  * that device current; make that first call before any stream capture. All calls share
  * the one array, so calls that overlap on the GPU (other streams, other threads) race:
  * serialise them. Results equal gpp_sigma's. Asynchronous on `stream`.
  */
-#define GPP_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+#define GPP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 GPP_API int gpp_sigma_noalloc(const gpp_problem *prob, const gpp_options *opt, void *stream);
 
 /* Gradients written by gpp_sigma_backward (device pointers; NULL skips that gradient). */

@@ -105,30 +105,20 @@ int check_pointers(const gpp_problem& p, int precision, bool outputs = true) {
   return GPP_OK;
 }
 
-int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan) {
+// Workspace layout of one instance. The gather segments come first; unless `gather_only`
+// (instances of a batched plan, the adjoint), the descriptor, tile counter and per-tile
+// partials of the main kernel follow.
+int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
+              bool gather_only = false) {
   gpp::FwdPlan pl;
   pl.nw = static_cast<int>(p.nw);
   pl.threads = o.block_threads ? o.block_threads : 128;
+  pl.igpt = o.ig_per_thread ? o.ig_per_thread : 4;
+  const bool f32 = o.precision == GPP_FP32_BULK;
   if (degenerate(p)) {
     *plan = pl;
     return GPP_OK;
   }
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "querying the device");
-  int bps = o.blocks_per_sm;
-  if (bps == 0) {
-    bps = (o.precision == GPP_FP32_BULK) ? gpp::fwd_f32_blocks_per_sm(pl.threads, pl.nw)
-                                         : gpp::fwd_f64_blocks_per_sm(pl.threads, pl.nw);
-    if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for %d threads", pl.threads);
-  }
-  pl.n_ig_tiles = (p.ncouls + pl.threads - 1) / pl.threads;
-  pl.ntiles = p.ngpown * pl.n_ig_tiles;
-  int64_t grid = static_cast<int64_t>(sms) * bps;
-  if (grid > pl.ntiles) grid = pl.ntiles;
-  if (grid < 1) grid = 1;
-  pl.grid = static_cast<int>(grid);
   size_t off = 0;
   pl.off_flags = off;
   off = gpp::align_up(off + 4 * sizeof(int));
@@ -138,18 +128,66 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan) {
   off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 4 * sizeof(double));
   pl.off_am = off;
   off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(double));
-  pl.off_partials = off;
-  off = gpp::align_up(off + static_cast<size_t>(pl.grid) * 4 * p.nw * sizeof(double));
-  if (o.precision == GPP_FP32_BULK) {
+  if (f32) {
     pl.off_bt32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 32);
     pl.off_am32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(float));
   }
+  pl.gather_total = off;
+  if (!gather_only) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "querying the device");
+    int bps = o.blocks_per_sm ? o.blocks_per_sm
+                              : gpp::batched_blocks_per_sm(pl.threads, pl.nw, f32);
+    if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for %d threads", pl.threads);
+    const int64_t tile_ig = static_cast<int64_t>(pl.threads) * pl.igpt;
+    pl.n_ig_tiles = (p.ncouls + tile_ig - 1) / tile_ig;
+    pl.ntiles = p.ngpown * pl.n_ig_tiles;
+    int64_t grid = static_cast<int64_t>(sms) * bps;
+    if (grid > pl.ntiles) grid = pl.ntiles;
+    if (grid < 1) grid = 1;
+    pl.grid = static_cast<int>(grid);
+    pl.off_desc = off;
+    off = gpp::align_up(off + sizeof(gpp::BatchInst));
+    pl.off_counter = off;
+    off = gpp::align_up(off + sizeof(unsigned long long));
+    pl.off_partials = off;
+    off = gpp::align_up(off + static_cast<size_t>(pl.ntiles) * 4 * p.nw * sizeof(double));
+  }
   pl.total = off;
   *plan = pl;
   return GPP_OK;
 }
+
+// The descriptor of a single instance whose gather segments start at `ws`.
+gpp::BatchInst describe(const gpp_problem& p, int occ_mode, bool f32, const gpp::FwdPlan& pl,
+                        char* ws) {
+  gpp::BatchInst d;
+  d.B = static_cast<int>(p.number_bands);
+  d.nocc = static_cast<int>(occ_mode == GPP_OCC_OCCUPIED ? std::min(p.nvband, p.number_bands)
+                                                         : p.number_bands);
+  d.G = p.ncouls;
+  d.P = p.ngpown;
+  d.n_ig_tiles = pl.n_ig_tiles;
+  d.aqsn = reinterpret_cast<const double2*>(p.aqsntemp);
+  d.aqsn32 = f32 ? reinterpret_cast<const float2*>(p.aqsntemp_c64) : nullptr;
+  d.eps = reinterpret_cast<const double2*>(p.I_eps_array);
+  d.wt = reinterpret_cast<const double2*>(p.wtilde_array);
+  d.am = reinterpret_cast<const double2*>(ws + pl.off_am);
+  d.am32 = f32 ? reinterpret_cast<const float2*>(ws + pl.off_am32) : nullptr;
+  d.bt = reinterpret_cast<const gpp::BandEntry*>(ws + pl.off_bt);
+  d.bt32 = f32 ? reinterpret_cast<const gpp::BandEntry32*>(ws + pl.off_bt32) : nullptr;
+  d.colg = reinterpret_cast<const int*>(ws + pl.off_colvalid);
+  d.flags = reinterpret_cast<const int*>(ws + pl.off_flags);
+  d.ach = p.achtemp;
+  d.asx = p.asxtemp;
+  return d;
+}
+
+int validate(const gpp_problem* prob, const gpp_options* opt, gpp_options* o);
 
 // Adjoint workspace: the gather segments of the forward layout (with a one-CTA partial
 // area), then the adjoint's band table, batch partials and per-(band, column) totals.
@@ -159,8 +197,7 @@ int make_bwd_plan(const gpp_problem& p, const gpp_options& o, gpp::BwdPlan* plan
   gpp::BwdPlan bp;
   gpp_options fo = o;
   fo.precision = GPP_FP64;
-  fo.blocks_per_sm = 1;
-  int rc = make_plan(p, fo, &bp.fwd);
+  int rc = make_plan(p, fo, &bp.fwd, true);
   if (rc) return rc;
   if (degenerate(p)) {
     *plan = bp;
@@ -236,8 +273,6 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
   if (rc) return rc;
   const gpp_problem& p = *prob;
   if ((rc = check_pointers(p, o.precision))) return rc;
-  if (o.precision == GPP_FP32_BULK && !gpp::fwd_f32_available())
-    return fail(GPP_ERR_UNSUPPORTED, "GPP_FP32_BULK is not built into this library");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (degenerate(p)) {
     cudaError_t e = cudaMemsetAsync(p.achtemp, 0, p.nw * sizeof(gpp_c128), s);
@@ -257,9 +292,13 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
   if (o.stage_events)
     for (int i = 0; i < 4; ++i) ev[i] = static_cast<cudaEvent_t>(o.stage_events[i]);
   auto mark = [&](int i) -> cudaError_t { return ev[i] ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+  const bool f32 = o.precision == GPP_FP32_BULK;
+  gpp::BatchInst desc = describe(p, o.occ_mode, f32, plan, ws);
+  desc.tile0 = 0;
+  desc.tile_end = plan.ntiles;
   cudaError_t e = mark(0);
   if (e != cudaSuccess) return cuda_fail(e, "recording stage event 0");
-  e = gpp::launch_prep(p, plan, ws, o.precision == GPP_FP32_BULK, s);
+  e = gpp::launch_prep(p, plan, ws, f32, &desc, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
   if (o.debug_checks) {
     int flags[4];
@@ -271,13 +310,14 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
                   flags[1]);
   }
   if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "recording stage event 1");
-  if (o.precision == GPP_FP64)
-    e = gpp::launch_fwd_f64(p, o.occ_mode, plan, ws, s);
-  else
-    e = gpp::launch_fwd_f32(p, o.occ_mode, plan, ws, s);
+  const gpp::BatchInst* dptr = reinterpret_cast<const gpp::BatchInst*>(ws + plan.off_desc);
+  double* partials = reinterpret_cast<double*>(ws + plan.off_partials);
+  e = gpp::launch_batched_main(dptr, 1, plan.ntiles, plan.nw, f32, plan.grid, plan.threads,
+                               plan.igpt, reinterpret_cast<unsigned long long*>(ws + plan.off_counter),
+                               partials, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the main sum");
   if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "recording stage event 2");
-  e = gpp::launch_reduce_final(plan, ws, p.achtemp, p.asxtemp, s);
+  e = gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the final reduction");
   if ((e = mark(3)) != cudaSuccess) return cuda_fail(e, "recording stage event 3");
   if (o.debug_checks) {
@@ -332,7 +372,7 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
     return fail(GPP_ERR_WORKSPACE, "adjoint workspace must be 256-byte aligned with %zu bytes",
                 plan.total);
   char* ws = static_cast<char*>(workspace);
-  cudaError_t e = gpp::launch_prep(p, plan.fwd, ws, false, s);
+  cudaError_t e = gpp::launch_prep(p, plan.fwd, ws, false, nullptr, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
   if (o.debug_checks) {
     int flags[4];
@@ -377,10 +417,8 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   bp->n = n;
   bp->nw = static_cast<int>(probs[0].nw);
   bp->f32 = o.precision == GPP_FP32_BULK;
-  if (bp->f32 && !gpp::fwd_f32_available())
-    return fail(GPP_ERR_UNSUPPORTED, "GPP_FP32_BULK is not built into this library");
   bp->threads = o.block_threads ? o.block_threads : 128;
-  bp->igpt = o.ig_per_thread ? o.ig_per_thread : 1;
+  bp->igpt = o.ig_per_thread ? o.ig_per_thread : 4;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -392,15 +430,13 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   bp->iplan.resize(n);
   bp->ioff.resize(n);
   size_t off = 0;
-  gpp_options io = o;
-  io.blocks_per_sm = 1;
   for (int i = 0; i < n; ++i) {
     const gpp_problem& p = probs[i];
     if ((rc = check_sizes(p))) return rc;
     if (p.nw != bp->nw) return fail(GPP_ERR_BAD_SIZE, "instance %d has nw %lld, instance 0 has %d", i, (long long)p.nw, bp->nw);
     if (degenerate(p)) return fail(GPP_ERR_BAD_SIZE, "instance %d is empty (batched instances need B, P, G >= 1)", i);
     if (check_ptrs && (rc = check_pointers(p, o.precision))) return rc;
-    if ((rc = make_plan(p, io, &bp->iplan[i]))) return rc;
+    if ((rc = make_plan(p, o, &bp->iplan[i], true))) return rc;
     bp->ioff[i] = off;
     off = gpp::align_up(off + bp->iplan[i].total);
   }
@@ -417,12 +453,9 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
     const gpp_problem& p = probs[i];
     gpp::BatchInst& d = bp->inst[k];
     d.index = i;
-    d.B = static_cast<int>(p.number_bands);
-    d.nocc = static_cast<int>(o.occ_mode == GPP_OCC_OCCUPIED ? std::min(p.nvband, p.number_bands)
-                                                             : p.number_bands);
-    d.G = p.ncouls;
-    d.P = p.ngpown;
+    d.occ_mode = o.occ_mode;
     d.n_ig_tiles = (p.ncouls + per_tile_ig - 1) / per_tile_ig;
+    d.P = p.ngpown;
     d.tile0 = t0;
     t0 += d.P * d.n_ig_tiles;
     d.tile_end = t0;
@@ -446,34 +479,31 @@ int batched_bind(gpp_batched_plan* bp, void* workspace, size_t bytes) {
   for (int k = 0; k < bp->n; ++k) {
     gpp::BatchInst& d = bp->inst[k];
     const int i = d.index;
-    const gpp_problem& p = bp->probs[i];
-    const gpp::FwdPlan& pl = bp->iplan[i];
-    char* w = bp->ws + bp->ioff[i];
-    d.aqsn = reinterpret_cast<const double2*>(p.aqsntemp);
-    d.aqsn32 = reinterpret_cast<const float2*>(p.aqsntemp_c64);
-    d.eps = reinterpret_cast<const double2*>(p.I_eps_array);
-    d.wt = reinterpret_cast<const double2*>(p.wtilde_array);
-    d.am = reinterpret_cast<const double2*>(w + pl.off_am);
-    d.am32 = bp->f32 ? reinterpret_cast<const float2*>(w + pl.off_am32) : nullptr;
-    d.bt = reinterpret_cast<const gpp::BandEntry*>(w + pl.off_bt);
-    d.bt32 = bp->f32 ? reinterpret_cast<const gpp::BandEntry32*>(w + pl.off_bt32) : nullptr;
-    d.colg = reinterpret_cast<const int*>(w + pl.off_colvalid);
-    d.flags = reinterpret_cast<const int*>(w + pl.off_flags);
-    d.ach = p.achtemp;
-    d.asx = p.asxtemp;
+    gpp::FwdPlan pl = bp->iplan[i];
+    pl.n_ig_tiles = d.n_ig_tiles;
+    gpp::BatchInst full = describe(bp->probs[i], d.occ_mode, bp->f32, pl, bp->ws + bp->ioff[i]);
+    full.index = i;
+    full.tile0 = d.tile0;
+    full.tile_end = d.tile_end;
+    d = full;
   }
   return GPP_OK;
 }
 
 cudaError_t batched_enqueue(gpp_batched_plan* bp, cudaStream_t s) {
   for (int i = 0; i < bp->n; ++i) {
-    cudaError_t e = gpp::launch_prep(bp->probs[i], bp->iplan[i], bp->ws + bp->ioff[i], bp->f32, s);
+    cudaError_t e = gpp::launch_prep(bp->probs[i], bp->iplan[i], bp->ws + bp->ioff[i], bp->f32,
+                                     nullptr, s);
     if (e != cudaSuccess) return e;
   }
-  return gpp::launch_batched(reinterpret_cast<const gpp::BatchInst*>(bp->ws + bp->off_inst), bp->n,
-                             bp->ntiles, bp->nw, bp->f32, bp->grid, bp->threads, bp->igpt,
-                             reinterpret_cast<unsigned long long*>(bp->ws + bp->off_counter),
-                             reinterpret_cast<double*>(bp->ws + bp->off_partials), s);
+  const auto* inst = reinterpret_cast<const gpp::BatchInst*>(bp->ws + bp->off_inst);
+  double* partials = reinterpret_cast<double*>(bp->ws + bp->off_partials);
+  cudaError_t e = gpp::launch_batched_main(inst, bp->n, bp->ntiles, bp->nw, bp->f32, bp->grid,
+                                           bp->threads, bp->igpt,
+                                           reinterpret_cast<unsigned long long*>(bp->ws + bp->off_counter),
+                                           partials, s);
+  if (e != cudaSuccess) return e;
+  return gpp::launch_batched_reduce(inst, bp->n, bp->nw, bp->f32, partials, s);
 }
 
 }  // namespace

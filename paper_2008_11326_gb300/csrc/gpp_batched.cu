@@ -1,8 +1,11 @@
-// Batched GPP sums: many instances of uneven size in one persistent launch.
+// The main GPP sum: one persistent launch over the tiles of one or many instances (a
+// single gpp_sigma call is a batch of one).
 //
 // Work unit: a tile = one local column p of one instance x (threads * ig_per_thread)
 // G-vectors, all bands. Tiles of all instances form one list, ordered by instance band count
-// (largest first, so the longest tiles start first and the tail is short). CTAs of a
+// (largest first, so the longest tiles start first and the tail is short); within an
+// instance the G-vector tile varies slowest, so the tiles running at the same time share
+// the same slab of aqsntemp (all bands x the tile's G-vectors) through L2. CTAs of a
 // persistent grid take tiles from an atomic counter; the counter only schedules, and every
 // tile writes its own partial slot, so the result does not depend on which CTA ran which
 // tile. A per-instance kernel then sums the instance's tile partials in tile order. The
@@ -19,8 +22,14 @@ namespace gpp {
 
 namespace {
 
+// Tile partials: FP64 sums (double) for GPP_FP64; compensated FP32 pairs (float2, hi + lo)
+// for GPP_FP32_BULK, so that its main kernel needs no FP64 arithmetic outside the rare
+// exact-decision and near-pole branches. Both are 8 bytes per value.
+// The FP32-bulk instantiation is held to two 256-thread CTAs' worth of registers per SM
+// (128 per thread): it is latency-bound and loses more to lower occupancy than it gains
+// from more registers.
 template <int W, bool F32>
-__global__ void __launch_bounds__(256) gpp_batched_kernel(const BatchInst* __restrict__ inst,
+__global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const BatchInst* __restrict__ inst,
                                                           int ninst, int64_t ntiles, int igpt,
                                                           unsigned long long* counter,
                                                           double* __restrict__ partials) {
@@ -32,25 +41,29 @@ __global__ void __launch_bounds__(256) gpp_batched_kernel(const BatchInst* __res
     const int64_t t = s_t;
     __syncthreads();
     if (t >= ntiles) break;
-    int lo = 0, hi = ninst - 1;  // instance holding tile t (tile ranges are sorted)
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
+    int ilo = 0, ihi = ninst - 1;  // instance holding tile t (tile ranges are sorted)
+    while (ilo < ihi) {
+      const int mid = (ilo + ihi) >> 1;
       if (__ldg(&inst[mid].tile_end) > t)
-        hi = mid;
+        ihi = mid;
       else
-        lo = mid + 1;
+        ilo = mid + 1;
     }
-    const BatchInst& d = inst[lo];
+    const BatchInst& d = inst[ilo];
     const int B = d.B, nocc = d.nocc;
     const int64_t G = d.G;
     const int64_t local = t - d.tile0;
-    const int64_t p = local / d.n_ig_tiles;
-    const int64_t igt = local - p * d.n_ig_tiles;
+    const int64_t igt = local / d.P;
+    const int64_t p = local - igt * d.P;
     const bool col_ok = d.colg[p] >= 0;
     const bool x_fast = d.flags[0] == 0 && (!F32 || d.flags[2] == 0);
-    double acc[4 * W];
+    double acc[4 * W];                 // FP64 sums (GPP_FP64)
+    float hi[4 * W], lo[4 * W];        // compensated FP32 sums hi + lo (GPP_FP32_BULK)
 #pragma unroll
-    for (int k = 0; k < 4 * W; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 4 * W; ++k) {
+      acc[k] = 0.0;
+      hi[k] = lo[k] = 0.0f;
+    }
     for (int j = 0; j < igpt; ++j) {
       const int64_t ig = (igt * igpt + j) * blockDim.x + threadIdx.x;
       const bool live = ig < G && col_ok;
@@ -64,9 +77,24 @@ __global__ void __launch_bounds__(256) gpp_batched_kernel(const BatchInst* __res
       const bool fast_lane = w.x >= 0.0 && gt_nonneg(wabs2, kFastWabs2Lo) &&
                              lt_nonneg(wabs2, kFastWabs2Hi);
       const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
-      if (F32 && fast) {
-        band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
-                         w, I, acc);
+      if (F32) {
+        if (fast) {
+          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
+                           w, I, hi, lo);
+        } else {  // the general path in FP64, folded into the pairs
+          double a[4 * W];
+#pragma unroll
+          for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
+          const double Iwr = fma(I.x, w.x, -I.y * w.y);
+          const double Iwi = fma(I.x, w.y, I.y * w.x);
+          band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                              w.x, w.y, Iwr, Iwi, a);
+#pragma unroll
+          for (int k = 0; k < 4 * W; ++k) {
+            const float h = static_cast<float>(a[k]);
+            pair_add(hi[k], lo[k], h, static_cast<float>(a[k] - static_cast<double>(h)));
+          }
+        }
       } else {
         const double Iwr = fma(I.x, w.x, -I.y * w.y);
         const double Iwi = fma(I.x, w.y, I.y * w.x);
@@ -78,11 +106,16 @@ __global__ void __launch_bounds__(256) gpp_batched_kernel(const BatchInst* __res
                               w.x, w.y, Iwr, Iwi, acc);
       }
     }
-    block_partials<4 * W>(acc, red, partials + t * 4 * W);
+    if (F32)
+      block_pairs<4 * W>(hi, lo, reinterpret_cast<float2*>(red),
+                         reinterpret_cast<float2*>(partials) + t * 4 * W);
+    else
+      block_partials<4 * W>(acc, red, partials + t * 4 * W);
   }
 }
 
 // One CTA per instance: the instance's tile partials summed in tile order, then a tree.
+template <bool F32>
 __global__ void __launch_bounds__(256) gpp_batched_reduce_kernel(const BatchInst* __restrict__ inst,
                                                                  int nv,
                                                                  const double* __restrict__ part) {
@@ -91,7 +124,14 @@ __global__ void __launch_bounds__(256) gpp_batched_reduce_kernel(const BatchInst
   const int64_t n = d.tile_end - d.tile0;
   for (int k = 0; k < nv; ++k) {
     double v = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += 256) v += part[(d.tile0 + j) * nv + k];
+    for (int64_t j = threadIdx.x; j < n; j += 256) {
+      if (F32) {
+        const float2 q = reinterpret_cast<const float2*>(part)[(d.tile0 + j) * nv + k];
+        v += static_cast<double>(q.x) + static_cast<double>(q.y);
+      } else {
+        v += part[(d.tile0 + j) * nv + k];
+      }
+    }
     s[threadIdx.x] = v;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
@@ -138,9 +178,9 @@ int batched_blocks_per_sm(int threads, int nw, bool f32) {
   return n;
 }
 
-cudaError_t launch_batched(const BatchInst* inst, int ninst, int64_t ntiles, int nw, bool f32,
-                           int grid, int threads, int igpt, unsigned long long* counter,
-                           double* partials, cudaStream_t s) {
+cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles, int nw,
+                                bool f32, int grid, int threads, int igpt,
+                                unsigned long long* counter, double* partials, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
 #define GPP_BATCHED_LAUNCH(WV)                                                                    \
@@ -162,8 +202,15 @@ cudaError_t launch_batched(const BatchInst* inst, int ninst, int64_t ntiles, int
     default: return cudaErrorInvalidValue;
   }
 #undef GPP_BATCHED_LAUNCH
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  gpp_batched_reduce_kernel<<<ninst, 256, 0, s>>>(inst, 4 * nw, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_reduce(const BatchInst* inst, int ninst, int nw, bool f32,
+                                  const double* partials, cudaStream_t s) {
+  if (f32)
+    gpp_batched_reduce_kernel<true><<<ninst, 256, 0, s>>>(inst, 4 * nw, partials);
+  else
+    gpp_batched_reduce_kernel<false><<<ninst, 256, 0, s>>>(inst, 4 * nw, partials);
   return cudaGetLastError();
 }
 

@@ -170,8 +170,9 @@ __global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
   const int64_t ntiles = static_cast<int64_t>(ngroups) * n_ig_tiles;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int gl = static_cast<int>(t / n_ig_tiles);       // group within the batch
-    const int64_t igt = t - static_cast<int64_t>(gl) * n_ig_tiles;
+    // G-vector tile slowest, so the CTAs running together share one slab of aqsntemp
+    const int64_t igt = t / ngroups;
+    const int gl = static_cast<int>(t - igt * ngroups);       // group within the batch
     const int64_t p = (group0 + gl) * kTY + ty;
     const int64_t ig = igt * kTX + tx;
     const bool col_ok = p < P && colg[p] >= 0;

@@ -105,4 +105,44 @@ __device__ __forceinline__ void block_partials(double (&acc)[NV], double* red, d
   }
 }
 
+// Compensated FP32 pair arithmetic (hi + lo, |lo| << |hi|): (hi, lo) += (bh, bl) with
+// Knuth's TwoSum on the leading parts, so the pair carries about twice FP32's precision.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float v = s - hi;
+  const float e = (hi - (s - v)) + (bh - v);
+  lo = lo + bl + e;
+  hi = s;
+}
+
+// Per-CTA partial of NV compensated FP32 pairs: warp butterflies and a warp-order sum, all
+// with pair_add; `red` is shared memory of at least (blockDim/32) * NV float2.
+template <int NV>
+__device__ __forceinline__ void block_pairs(float (&hi)[NV], float (&lo)[NV], float2* red,
+                                            float2* out) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float h = hi[k], l = lo[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, off);
+      const float ol = __shfl_xor_sync(0xffffffffu, l, off);
+      pair_add(h, l, oh, ol);
+    }
+    if (lane == 0) red[warp * NV + k] = make_float2(h, l);
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    float h = 0.0f, l = 0.0f;
+    for (int w = 0; w < nwarps; ++w) {
+      const float2 v = red[w * NV + threadIdx.x];
+      pair_add(h, l, v.x, v.y);
+    }
+    out[threadIdx.x] = make_float2(h, l);
+  }
+}
+
 }  // namespace gpp

@@ -13,40 +13,37 @@ struct BandEntry;
 struct BandEntry32;
 
 // Layout of the caller's workspace for one forward call. Every segment starts on a
-// 256-byte boundary.
+// 256-byte boundary. With `gather_only` (instances of a batched plan, the adjoint) the
+// descriptor, counter and partial segments are empty.
 struct FwdPlan {
   int threads = 128;      // threads per CTA of the main kernel
-  int grid = 0;           // CTAs of the main kernel (a persistent, statically scheduled grid)
+  int igpt = 4;           // G-vectors per thread per tile
+  int grid = 0;           // CTAs of the persistent main kernel
   int nw = 0;
-  int64_t n_ig_tiles = 0; // ig tiles of `threads` G-vectors per column
+  int64_t n_ig_tiles = 0; // tiles per column: ceil(G / (threads * igpt))
   int64_t ntiles = 0;     // ngpown * n_ig_tiles
   size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count, [2] any |wx| >= 1e4
-  size_t off_colvalid = 0;// int32[P]
-  size_t off_bt = 0;      // band table double4[B][W] = {x, x^2, 4x, 0}
+  size_t off_colvalid = 0;// int32[P]: global column of each local column, or -1
+  size_t off_bt = 0;      // band table BandEntry[B][W] = {x, x^2, 4x, -x/2}
   size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
-  size_t off_partials = 0;// double[grid][4 W]
   size_t off_bt32 = 0;    // FP32-bulk only: BandEntry32[B][W]
   size_t off_am32 = 0;    // FP32-bulk only: gathered weights c64[P][B]
+  size_t gather_total = 0;
+  size_t off_desc = 0;    // the instance descriptor (BatchInst)
+  size_t off_counter = 0; // tile counter
+  size_t off_partials = 0;// 8 bytes x [ntiles][4 W]: double (FP64) or float2 (FP32-bulk)
   size_t total = 0;
 };
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Main-kernel CTAs that fit on one SM (occupancy query; 0 on error).
-int fwd_f64_blocks_per_sm(int threads, int nw);
-int fwd_f32_blocks_per_sm(int threads, int nw);
-bool fwd_f32_available();
+struct BatchInst;
 
-// Column gather, band table and index checks (one kernel).
+// Column gather, band tables and index checks (one kernel); with `desc` it also writes the
+// single-instance descriptor to plan.off_desc.
 cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
-                        cudaStream_t s);
-// Main sum in FP64 (writes per-CTA partials).
-cudaError_t launch_fwd_f64(const gpp_problem& p, int occ_mode, const FwdPlan& plan, char* ws,
-                           cudaStream_t s);
-// Main sum with FP32 bulk arithmetic (writes per-CTA partials in FP64).
-cudaError_t launch_fwd_f32(const gpp_problem& p, int occ_mode, const FwdPlan& plan, char* ws,
-                           cudaStream_t s);
+                        const BatchInst* desc, cudaStream_t s);
 // Workspace of the adjoint: the forward's gather segments plus the batch partials.
 struct BwdPlan {
   FwdPlan fwd;             // flags, colvalid, band table, gathered weights
@@ -70,8 +67,8 @@ cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, 
 // One instance of a batched launch (device-resident descriptor; see gpp_batched.cu).
 struct BatchInst {
   int B = 0, nocc = 0;
-  int index = 0;  // position of the instance in the caller's array
-  int pad = 0;
+  int index = 0;     // position of the instance in the caller's array
+  int occ_mode = 0;  // host-side bookkeeping while a batch is laid out
   int64_t G = 0, P = 0, n_ig_tiles = 0, tile0 = 0, tile_end = 0;
   const double2* aqsn = nullptr;
   const float2* aqsn32 = nullptr;
@@ -88,17 +85,17 @@ struct BatchInst {
 };
 
 int batched_blocks_per_sm(int threads, int nw, bool f32);
-// Resets the tile counter, runs the persistent kernel and the per-instance reduction.
-cudaError_t launch_batched(const BatchInst* inst, int ninst, int64_t ntiles, int nw, bool f32,
-                           int grid, int threads, int igpt, unsigned long long* counter,
-                           double* partials, cudaStream_t s);
+// Resets the tile counter and runs the persistent main kernel.
+cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles, int nw,
+                                bool f32, int grid, int threads, int igpt,
+                                unsigned long long* counter, double* partials, cudaStream_t s);
+// Per-instance fixed-order sum of the tile partials into the outputs.
+cudaError_t launch_batched_reduce(const BatchInst* inst, int ninst, int nw, bool f32,
+                                  const double* partials, cudaStream_t s);
 
 // Sets the thread-local message returned by gpp_last_error(); returns `code`.
 int report_error(int code, const char* msg);
 void clear_error();
 
-// Fixed-order reduction of the partials into achtemp / asxtemp.
-cudaError_t launch_reduce_final(const FwdPlan& plan, char* ws, gpp_c128* ach, gpp_c128* asx,
-                                cudaStream_t s);
 
 }  // namespace gpp

@@ -1,5 +1,29 @@
-// The FP32-bulk per-band evaluation (shared by the single-instance and batched kernels).
-// The precision choices are described at the top of gpp_fwd_f32.cu.
+// The FP32-bulk per-band evaluation (GPP_FP32_BULK), used by the main kernel
+// (gpp_batched.cu).
+//
+// Same decomposition and algebra as the FP64 path (gpp_fwd.cu, gpp_terms_f64.cuh), with the per-term
+// complex arithmetic in FP32 on complex64 data: the band-indexed aqsntemp is read from
+// its complex64 copy and the gathered weights conj(aqsmtemp) vcoul are rounded once by
+// the gather kernel; wtilde and I_eps are read in FP64 once per (igp, ig) pair and rounded
+// in registers. FP64 is kept where FP32 would change the answer:
+//
+//  * Branch decisions. The branch taken at |wdiff|^2 = 1/4 is discontinuous, and FP32
+//    rounding of x and w moves |wdiff|^2 by ~1e-7: on the benchmark shape thousands of
+//    terms would switch branch, an error of order 1e-4 in the sums. The kernel therefore
+//    evaluates d = |wdiff|^2 - 1/4 in FP32 together with a bound m on its rounding error,
+//        m = 2^-20 (|x| + |Re w| + 2),
+//    which is at least three times the worst-case error of the FP32 value when |d| < 0.1
+//    and |x| < 1e4 (and larger |d| are always decided correctly). If |d| > m the FP32 sign
+//    of d is the FP64 decision; otherwise (a fraction ~1e-6 of the terms) the lane
+//    recomputes |wdiff|^2 in FP64 exactly as the FP64 kernel does. Every branch decision
+//    is therefore the FP64 kernel's.
+//  * The pole |wdiff| -> 0. There the FP32 product |wdiff|^2 |x + w|^2 can underflow; for
+//    |wdiff|^2 < 2^-30 the branch-2 coefficient 1/|x + w|^2 is taken in FP64.
+//  * Accumulation. Terms are summed in FP32 over chunks of kChunk bands, chunk sums are
+//    added into compensated (Kahan) FP32 pairs, the pairs are folded into FP64 at the end
+//    of every tile, and the block and final reductions are FP64 (gpp_fwd.cu).
+//  * Inputs outside the fast path's range (negative frequencies, Re w < 0, |w|^2 outside
+//    (1e-12, 62499), |x| >= 1e4) are evaluated by the FP64 general path for the whole warp.
 #pragma once
 
 #include "gpp_device.cuh"
@@ -116,13 +140,17 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
   }
 }
 
+// All bands of one (igp, ig) pair into the caller's compensated FP32 pairs (hi + lo): bands
+// are summed in FP32 over chunks of kChunk bands and every chunk sum is added to the pair
+// with Kahan's compensation.
 template <int W>
 __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
                                               const float2* __restrict__ an_ptr,
                                               const float2* __restrict__ am_ptr,
                                               const BandEntry32* __restrict__ bt32,
                                               const BandEntry* __restrict__ bt64,
-                                              double2 w64, double2 I64, double (&acc)[4 * W]) {
+                                              double2 w64, double2 I64, float (&hi)[4 * W],
+                                              float (&lo)[4 * W]) {
   PairF32 q;
   q.wr = static_cast<float>(w64.x);
   q.wi = static_cast<float>(w64.y);
@@ -137,9 +165,6 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
   q.wm = kMarginScale * fabsf(q.wr);
   q.wr64 = w64.x;
   q.wi2_64 = w64.y * w64.y;
-  float hi[4 * W], lo[4 * W];
-#pragma unroll
-  for (int k = 0; k < 4 * W; ++k) hi[k] = lo[k] = 0.0f;
 #pragma unroll 1
   for (int b0 = 0; b0 < B; b0 += kChunk) {
     float c[4 * W];
@@ -149,18 +174,15 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
     bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, bt64, q, c);
     if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, bt64, q, c);
-    // Kahan merge of the chunk sums: hi + lo carries the running sum, lo the lost low part
+    // Kahan merge of the chunk sums; the pair holds the running sum as hi + lo
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) {
-      const float y = c[k] - lo[k];
+      const float y = c[k] + lo[k];
       const float t = hi[k] + y;
-      lo[k] = (t - hi[k]) - y;
+      lo[k] = y - (t - hi[k]);
       hi[k] = t;
     }
   }
-#pragma unroll
-  for (int k = 0; k < 4 * W; ++k)
-    acc[k] += static_cast<double>(hi[k]) - static_cast<double>(lo[k]);
 }
 
 }  // namespace gpp

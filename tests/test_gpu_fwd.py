@@ -140,6 +140,9 @@ def test_deterministic_and_launch_shapes(gpp):
         for bps in (0, 1, 3):
             got = run(gpp, prob, block_threads=bt, blocks_per_sm=bps)
             assert rel_err(got, ref) <= RTOL, (bt, bps)
+    for k in (1, 2, 3, 8):
+        got = run(gpp, prob, ig_per_thread=k)
+        assert rel_err(got, ref) <= RTOL, k
 
 
 def test_empty_problems(gpp):
