@@ -110,6 +110,19 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
       c2 = gt_nonneg(wabs2, kTolZero * A2);
     }
     const double r = rcp_refined(A2 * S2);
+    if (__all_sync(0xffffffffu, c1)) {
+      // every lane on branch 1: u = 1/(x - w), uv = 1/(x^2 - w^2)
+      const double2 u = make_double2(Ar * (S2 * r), wi * (S2 * r));
+      cmac(GI, __ldg(&e[iw].ca), u);
+      cmac(GW, __ldg(&e[iw].cax), cmul(u, u));
+      if (OCC) {
+        const double2 uv = make_double2((x2 + mw2r) * r, w2i * r);
+        const double2 wuv = cmul(w, uv);
+        cmac(GI, __ldg(&e[iw].cs), wuv);
+        cmac(GW, __ldg(&e[iw].cs2x2), cmul(wuv, uv));
+      }
+      continue;
+    }
     const double a1 = c1 ? S2 * r : 0.0;
     const double2 u = make_double2(Ar * a1, wi * a1);          // 1/(x - w) on branch 1
     cmac(GI, __ldg(&e[iw].ca), u);
