@@ -139,6 +139,7 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = gpp::batched_prepare(pl.threads, pl.nw, f32);
     if (e != cudaSuccess) return cuda_fail(e, "querying the device");
     int bps = o.blocks_per_sm ? o.blocks_per_sm
                               : gpp::batched_blocks_per_sm(pl.threads, pl.nw, f32);
@@ -422,6 +423,7 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = gpp::batched_prepare(bp->threads, bp->nw, bp->f32);
   if (e != cudaSuccess) return cuda_fail(e, "querying the device");
   int bps = o.blocks_per_sm ? o.blocks_per_sm : gpp::batched_blocks_per_sm(bp->threads, bp->nw, bp->f32);
   if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for the batched kernel");

@@ -25,16 +25,23 @@ namespace {
 // Tile partials: FP64 sums (double) for GPP_FP64; compensated FP32 pairs (float2, hi + lo)
 // for GPP_FP32_BULK, so that its main kernel needs no FP64 arithmetic outside the rare
 // exact-decision and near-pole branches. Both are 8 bytes per value.
-// The FP32-bulk instantiation is held to two 256-thread CTAs' worth of registers per SM
-// (128 per thread): it is latency-bound and loses more to lower occupancy than it gains
-// from more registers.
+// The FP32-bulk instantiation is held to 64 registers per thread (four 256-thread CTAs per
+// SM; 80 for nw > 5, whose band loop would spill at 64): it is latency-bound, and on GB300
+// (nw = 3) it ran 253 ms at 128 registers, 178 ms at 80 and 150 ms at 64 on the benchmark
+// shape (its compensated pairs live in shared memory, and only the rare FP64 fallback path
+// spills at this budget).
 template <int W, bool F32>
-__global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const BatchInst* __restrict__ inst,
+__global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_kernel(const BatchInst* __restrict__ inst,
                                                           int ninst, int64_t ntiles, int igpt,
                                                           unsigned long long* counter,
                                                           double* __restrict__ partials) {
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
+  // FP32-bulk: the threads' compensated pairs, [2][4W][blockDim.x] floats, and their FP64
+  // wtilde, double2[blockDim.x], and the FP64 band table pointer (dynamic shared memory of
+  // batched_smem_bytes)
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  float* const s_pair = reinterpret_cast<float*>(dyn_smem);
   for (;;) {
     if (threadIdx.x == 0) s_t = static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
@@ -58,11 +65,11 @@ __global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const Bat
     const bool col_ok = d.colg[p] >= 0;
     const bool x_fast = d.flags[0] == 0 && (!F32 || d.flags[2] == 0);
     double acc[4 * W];                 // FP64 sums (GPP_FP64)
-    float hi[4 * W], lo[4 * W];        // compensated FP32 sums hi + lo (GPP_FP32_BULK)
 #pragma unroll
-    for (int k = 0; k < 4 * W; ++k) {
-      acc[k] = 0.0;
-      hi[k] = lo[k] = 0.0f;
+    for (int k = 0; k < 4 * W; ++k) acc[k] = 0.0;
+    if (F32) {
+#pragma unroll
+      for (int k = 0; k < 2 * 4 * W; ++k) s_pair[k * blockDim.x + threadIdx.x] = 0.0f;
     }
     for (int j = 0; j < igpt; ++j) {
       const int64_t ig = (igt * igpt + j) * blockDim.x + threadIdx.x;
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const Bat
       if (F32) {
         if (fast) {
           band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
-                           w, I, hi, lo);
+                           w, I, live, s_pair);
         } else {  // the general path in FP64, folded into the pairs
           double a[4 * W];
 #pragma unroll
@@ -92,7 +99,9 @@ __global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const Bat
 #pragma unroll
           for (int k = 0; k < 4 * W; ++k) {
             const float h = static_cast<float>(a[k]);
-            pair_add(hi[k], lo[k], h, static_cast<float>(a[k] - static_cast<double>(h)));
+            float& ph = s_pair[k * blockDim.x + threadIdx.x];
+            float& pl = s_pair[(4 * W + k) * blockDim.x + threadIdx.x];
+            pair_add(ph, pl, h, static_cast<float>(a[k] - static_cast<double>(h)));
           }
         }
       } else {
@@ -106,9 +115,16 @@ __global__ void __launch_bounds__(256, F32 ? 2 : 1) gpp_batched_kernel(const Bat
                               w.x, w.y, Iwr, Iwi, acc);
       }
     }
-    if (F32)
+    if (F32) {
+      float hi[4 * W], lo[4 * W];
+#pragma unroll
+      for (int k = 0; k < 4 * W; ++k) {
+        hi[k] = s_pair[k * blockDim.x + threadIdx.x];
+        lo[k] = s_pair[(4 * W + k) * blockDim.x + threadIdx.x];
+      }
       block_pairs<4 * W>(hi, lo, reinterpret_cast<float2*>(red),
                          reinterpret_cast<float2*>(partials) + t * 4 * W);
+    }
     else
       block_partials<4 * W>(acc, red, partials + t * 4 * W);
   }
@@ -170,11 +186,32 @@ const void* batched_kernel_ptr(int nw, bool f32) {
 
 }  // namespace
 
+size_t batched_smem_bytes(int threads, int nw, bool f32) {
+  return f32 ? static_cast<size_t>(threads) * (2 * 4 * nw * sizeof(float) + 2 * sizeof(double) +
+                                               sizeof(void*))
+             : 0;
+}
+
+// A CTA whose static + dynamic shared memory exceeds 48 KB (nw >= 6 at 256 threads) must
+// opt in; the kernel's static part (the reduction buffer) is below 4 KB. Called at plan
+// time, outside any stream capture.
+cudaError_t batched_prepare(int threads, int nw, bool f32) {
+  const void* fn = batched_kernel_ptr(nw, f32);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = batched_smem_bytes(threads, nw, f32);
+  if (smem + 4096 <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(smem));
+}
+
 int batched_blocks_per_sm(int threads, int nw, bool f32) {
   const void* fn = batched_kernel_ptr(nw, f32);
   if (!fn) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads,
+                                                    batched_smem_bytes(threads, nw, f32)) !=
+      cudaSuccess)
+    return 0;
   return n;
 }
 
@@ -183,10 +220,11 @@ cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles
                                 unsigned long long* counter, double* partials, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  const size_t smem = batched_smem_bytes(threads, nw, f32);
 #define GPP_BATCHED_LAUNCH(WV)                                                                    \
   if (f32)                                                                                        \
-    gpp_batched_kernel<WV, true><<<grid, threads, 0, s>>>(inst, ninst, ntiles, igpt, counter,     \
-                                                          partials);                              \
+    gpp_batched_kernel<WV, true><<<grid, threads, smem, s>>>(inst, ninst, ntiles, igpt, counter,  \
+                                                             partials);                           \
   else                                                                                            \
     gpp_batched_kernel<WV, false><<<grid, threads, 0, s>>>(inst, ninst, ntiles, igpt, counter,    \
                                                            partials)

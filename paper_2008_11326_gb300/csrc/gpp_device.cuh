@@ -31,18 +31,20 @@ struct alignas(32) BandEntry {
 };
 
 // The FP32 band table entry: x, x^2, 4x, -x/2 rounded to FP32, and the part of the
-// branch-decision margin that depends on x (see gpp_fwd_f32.cu).
+// branch-decision margin that depends on x (see gpp_terms_f32.cuh).
 struct alignas(32) BandEntry32 {
   float4 a;  // x, x^2, 4x, -x/2
-  float4 b;  // margin_x, 0, 0, 0
+  float4 b;  // x rounded down, x rounded up, margin_x, 0
 };
 
 // Flags written by the gather kernel: [0] some wx < 0 or NaN, [1] bad index count,
 // [2] some |wx| >= kFp32MaxX or NaN (the FP32 decision margin assumes smaller x).
 constexpr double kFp32MaxX = 1.0e4;
 
-// Scale of the FP32 branch-decision margin, 2^-20 (see gpp_fwd_f32.cu).
+// The FP32 branch-decision margin 2^-20 (|x| + kMarginW) (see gpp_terms_f32.cuh); kMarginW
+// bounds |Re w| + 2 on the fast path, where |w|^2 < kFastWabs2Hi.
 constexpr float kMarginScale = 9.5367431640625e-07f;
+constexpr float kMarginW = 252.0f;
 
 // Ordering of non-negative doubles equals the ordering of their bit patterns as signed
 // 64-bit integers. The comparisons below run on the integer pipe instead of the FP64 pipe

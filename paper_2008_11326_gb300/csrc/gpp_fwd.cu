@@ -86,7 +86,8 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
       const float xf = static_cast<float>(x);
       BandEntry32 e;
       e.a = make_float4(xf, static_cast<float>(x * x), 4.0f * xf, -0.5f * xf);
-      e.b = make_float4(kMarginScale * (fabsf(xf) + 2.0f), 0.0f, 0.0f, 0.0f);
+      e.b = make_float4(__double2float_rd(x), __double2float_ru(x),
+                        kMarginScale * (fabsf(xf) + kMarginW), 0.0f);
       bt32[i] = e;
     }
   }

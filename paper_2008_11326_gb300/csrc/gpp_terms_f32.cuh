@@ -11,7 +11,7 @@
 //    rounding of x and w moves |wdiff|^2 by ~1e-7: on the benchmark shape thousands of
 //    terms would switch branch, an error of order 1e-4 in the sums. The kernel therefore
 //    evaluates d = |wdiff|^2 - 1/4 in FP32 together with a bound m on its rounding error,
-//        m = 2^-20 (|x| + |Re w| + 2),
+//        m = 2^-20 (|x| + 252)  >=  2^-20 (|x| + |Re w| + 2)   (|Re w| < 250 on the fast path),
 //    which is at least three times the worst-case error of the FP32 value when |d| < 0.1
 //    and |x| < 1e4 (and larger |d| are always decided correctly). If |d| > m the FP32 sign
 //    of d is the FP64 decision; otherwise (a fraction ~1e-6 of the terms) the lane
@@ -24,6 +24,14 @@
 //    of every tile, and the block and final reductions are FP64 (gpp_fwd.cu).
 //  * Inputs outside the fast path's range (negative frequencies, Re w < 0, |w|^2 outside
 //    (1e-12, 62499), |x| >= 1e4) are evaluated by the FP64 general path for the whole warp.
+//
+// Most terms are far from the threshold: a warp's 32 G-vectors span an interval of Re w,
+// and a frequency x more than 1/2 + 2^-20 outside [min Re w, max Re w] is on branch 1 for
+// every lane (|wdiff| >= |x - Re w| > 1/2, and 2^-20 exceeds every FP64 rounding of
+// |wdiff|^2 near 1/4 for |x| < 1e4), whatever FP32 gives. The kernel forms that interval
+// once per (igp, ig) pair with directed rounding and tests x rounded down and up against it
+// (two comparisons, the same for the whole warp); such terms skip the decision, the
+// margin test, the pole test and both warp votes.
 #pragma once
 
 #include "gpp_device.cuh"
@@ -54,8 +62,25 @@ __device__ __forceinline__ float isel(bool c, float a, float b) {
 
 // Per-(igp, ig) constants of the FP32 path.
 struct PairF32 {
-  float wr, wi, wi2, mw2r, w2i, wrh, wih, Iwr, Iwi, wm;
-  double wr64, wi2_64;
+  float wr, wi, wi2, mw2r, w2i, Iwr, Iwi;
+  float lo, hi;  // the warp's interval [min Re w - 1/2, max Re w + 1/2], widened by 2^-20
+};
+
+// The thread's slots in the FP32 path's shared memory (layout in band_loop_f32): the
+// compensated pairs, the FP64 wtilde and the FP64 band table of the instance, the last two
+// read only on the rare exact-decision path (kept there rather than in registers).
+template <int W>
+struct F32Slots {
+  static __device__ __forceinline__ float* pair(float* sp, int k) {
+    return sp + k * blockDim.x + threadIdx.x;
+  }
+  static __device__ __forceinline__ double2* w64(float* sp) {
+    return reinterpret_cast<double2*>(sp + 2 * 4 * W * blockDim.x) + threadIdx.x;
+  }
+  static __device__ __forceinline__ const BandEntry** bt64(float* sp) {
+    return reinterpret_cast<const BandEntry**>(sp + 2 * 4 * W * blockDim.x + 4 * blockDim.x) +
+           threadIdx.x;
+  }
 };
 
 // Bands [b0, b1) into the chunk sums c. OCC (whether these bands enter asxtemp) is a
@@ -63,14 +88,22 @@ struct PairF32 {
 template <int W, bool OCC>
 __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float2* __restrict__ an_ptr,
                                           const float2* __restrict__ am_ptr,
-                                          const BandEntry32* __restrict__ bt32,
-                                          const BandEntry* __restrict__ bt64, const PairF32& q,
-                                          float (&c)[4 * W]) {
+                                          const BandEntry32* __restrict__ bt32, float* sp,
+                                          const PairF32& q, float (&c)[4 * W]) {
+  if (b0 >= b1) return;
+  // the next band's aqsntemp and weight are loaded one band ahead (their global-memory
+  // latency is the kernel's main stall); inert lanes read a valid element, and their I = 0
+  // makes every product vanish
+  float2 an_next = ldgf2(an_ptr + static_cast<int64_t>(b0) * G);
+  float2 am_next = ldgf2(am_ptr + b0);
 #pragma unroll 1
   for (int b = b0; b < b1; ++b) {
-    // inert lanes read a valid element; their I = 0 makes every product vanish
-    const float2 an = ldgf2(an_ptr + static_cast<int64_t>(b) * G);
-    const float2 am = ldgf2(am_ptr + b);
+    const float2 an = an_next;
+    const float2 am = am_next;
+    if (b + 1 < b1) {
+      an_next = ldgf2(an_ptr + static_cast<int64_t>(b + 1) * G);
+      am_next = ldgf2(am_ptr + b + 1);
+    }
     const float Mr = fmaf(am.x, an.x, -am.y * an.y);
     const float Mi = fmaf(am.x, an.y, am.y * an.x);
     const float Kr = fmaf(Mr, q.Iwr, -Mi * q.Iwi);
@@ -83,35 +116,53 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
 #pragma unroll
     for (int iw = 0; iw < W; ++iw) {
       const float4 ea = __ldg(&e[iw].a);
-      const float xm = __ldg(&e[iw].b.x);
-      const float x = ea.x, x2 = ea.y, x4 = ea.z, xh = ea.w;
+      const float4 eb = __ldg(&e[iw].b);
+      const float x = ea.x, x2 = ea.y, x4 = ea.z;
       const float Ar = x - q.wr;
       const float A2 = fmaf(Ar, Ar, q.wi2);
       const float S2 = fmaf(x4, q.wr, A2);
       float r = rcp_approx_f32(A2 * S2);
+      const float tr = fmaf(Kr, Ar, Kwr);
+      const float ti = fmaf(Ki, Ar, Kwi);
+      if (eb.x > q.hi || eb.y < q.lo) {
+        // x outside the warp's interval: branch 1 for every lane, K conj(A) / |A|^2 and
+        // K2 conj(C) / |C|^2
+        const float a1 = S2 * r;
+        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
+        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+        if (OCC) {
+          const float Yr = x2 + q.mw2r;
+          const float ur = fmaf(K2r, Yr, P1r);
+          const float ui = fmaf(K2i, Yr, P1i);
+          c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
+          c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
+        }
+        continue;
+      }
       float b2 = A2 * r;
       const float d = A2 - 0.25f;
       bool c1 = d > 0.0f;
-      const bool near = fabsf(d) <= xm + q.wm;
+      const bool near = fabsf(d) <= eb.z;
       const bool pole = A2 < kPoleA2;
       if (__any_sync(0xffffffffu, near || pole)) {
         if (near || pole) {
+          const BandEntry* bt64 = *F32Slots<W>::bt64(sp);
           const double x64 = __ldg(&bt64[static_cast<int64_t>(b) * W + iw].lo.x);
+          const double2 w64 = *F32Slots<W>::w64(sp);
+          const double wi2_64 = w64.y * w64.y;
           if (near) {  // decide exactly as the FP64 kernel
-            const double a64 = x64 - q.wr64;
-            c1 = gt_nonneg(fma(a64, a64, q.wi2_64), kLimitTwo);
+            const double a64 = x64 - w64.x;
+            c1 = gt_nonneg(fma(a64, a64, wi2_64), kLimitTwo);
           }
           if (pole) {  // 1/|x + w|^2 in FP64 next to the pole; r only feeds branch 1
-            const double s64 = x64 + q.wr64;
-            b2 = static_cast<float>(rcp_refined(fma(s64, s64, q.wi2_64)));
+            const double s64 = x64 + w64.x;
+            b2 = static_cast<float>(rcp_refined(fma(s64, s64, wi2_64)));
             r = 0.0f;
           }
         }
       }
-      const float tr = fmaf(Kr, Ar, Kwr);
-      const float ti = fmaf(Ki, Ar, Kwi);
       if (__all_sync(0xffffffffu, c1)) {
-        // every lane on branch 1: K conj(A) / |A|^2 and K2 conj(C) / |C|^2
+        // every lane on branch 1
         const float a1 = S2 * r;
         c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
         c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
@@ -128,10 +179,11 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
         c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
         if (OCC) {
           // branch 2: K (-conj(S)/2) / |S|^2 = (Re K Yr - Im K Im w/2, Im K Yr + Re K Im w/2) b2
+          const float wih = 0.5f * q.wi;
           const float coef = isel(c1, r, b2);
-          const float Yr = isel(c1, x2, xh) + isel(c1, q.mw2r, q.wrh);
-          const float ur = fmaf(isel(c1, K2r, Kr), Yr, isel(c1, P1r, -Ki * q.wih));
-          const float ui = fmaf(isel(c1, K2i, Ki), Yr, isel(c1, P1i, Kr * q.wih));
+          const float Yr = isel(c1, x2, ea.w) + isel(c1, q.mw2r, -0.5f * q.wr);
+          const float ur = fmaf(isel(c1, K2r, Kr), Yr, isel(c1, P1r, -Ki * wih));
+          const float ui = fmaf(isel(c1, K2i, Ki), Yr, isel(c1, P1i, Kr * wih));
           c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
           c[4 * iw + 3] = fmaf(ui, coef, c[4 * iw + 3]);
         }
@@ -140,17 +192,21 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
   }
 }
 
-// All bands of one (igp, ig) pair into the caller's compensated FP32 pairs (hi + lo): bands
-// are summed in FP32 over chunks of kChunk bands and every chunk sum is added to the pair
-// with Kahan's compensation.
+// All bands of one (igp, ig) pair into the thread's compensated FP32 pairs hi + lo, which
+// live in shared memory (`sp`, layout [2][4W][blockDim.x] floats, then the threads' FP64
+// wtilde as double2[blockDim.x], then the FP64 band table pointer [blockDim.x]: touched once
+// per chunk, or only on the rare exact-decision path, they would otherwise hold registers
+// through the band loop, and the FP32 path is limited by occupancy). Bands are summed in
+// FP32 over chunks of kChunk bands and every chunk sum is added to the pair with Kahan's
+// compensation.
 template <int W>
 __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
                                               const float2* __restrict__ an_ptr,
                                               const float2* __restrict__ am_ptr,
                                               const BandEntry32* __restrict__ bt32,
                                               const BandEntry* __restrict__ bt64,
-                                              double2 w64, double2 I64, float (&hi)[4 * W],
-                                              float (&lo)[4 * W]) {
+                                              double2 w64, double2 I64, bool live,
+                                              float* sp) {
   PairF32 q;
   q.wr = static_cast<float>(w64.x);
   q.wi = static_cast<float>(w64.y);
@@ -158,13 +214,25 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
   q.wi2 = q.wi * q.wi;
   q.mw2r = -fmaf(q.wr, q.wr, -q.wi2);   // -Re w^2
   q.w2i = 2.0f * q.wr * q.wi;           // Im w^2
-  q.wrh = -0.5f * q.wr;
-  q.wih = 0.5f * q.wi;
   q.Iwr = fmaf(Ir, q.wr, -Ii * q.wi);
   q.Iwi = fmaf(Ir, q.wi, Ii * q.wr);
-  q.wm = kMarginScale * fabsf(q.wr);
-  q.wr64 = w64.x;
-  q.wi2_64 = w64.y * w64.y;
+  *F32Slots<W>::w64(sp) = w64;
+  *F32Slots<W>::bt64(sp) = bt64;
+  {  // the warp's Re w interval (inert lanes, whose I is 0, left out)
+    constexpr double kHalf = 0.5 + 9.5367431640625e-07;  // 1/2 + 2^-20
+    float lo = __double2float_rd(w64.x - kHalf), hi = __double2float_ru(w64.x + kHalf);
+    if (!live) {
+      lo = __int_as_float(0x7f800000);   // +inf
+      hi = -lo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    q.lo = lo;
+    q.hi = hi;
+  }
 #pragma unroll 1
   for (int b0 = 0; b0 < B; b0 += kChunk) {
     float c[4 * W];
@@ -172,15 +240,17 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
     const int bend = min(b0 + kChunk, B);
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
-    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, bt64, q, c);
-    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, bt64, q, c);
+    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, sp, q, c);
+    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, sp, q, c);
     // Kahan merge of the chunk sums; the pair holds the running sum as hi + lo
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) {
-      const float y = c[k] + lo[k];
-      const float t = hi[k] + y;
-      lo[k] = y - (t - hi[k]);
-      hi[k] = t;
+      float& hi = *F32Slots<W>::pair(sp, k);
+      float& lo = *F32Slots<W>::pair(sp, 4 * W + k);
+      const float y = c[k] + lo;
+      const float t = hi + y;
+      lo = y - (t - hi);
+      hi = t;
     }
   }
 }

@@ -95,6 +95,17 @@ def test_deterministic(gpp):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("nw", [1, 6, 7, 8])
+def test_launch_shapes(gpp, nw):
+    """Every CTA size and tile depth; at nw >= 7 and 256 threads the compensated pairs
+    need more than 48 KB of shared memory per CTA."""
+    prob = inputs.make_problem(37, 2, 900, 5, nw, seed=60 + nw)
+    ref = oracle.sigma(prob)
+    for bt in (64, 96, 128, 256):
+        for k in (1, 4):
+            assert rel_err(run(gpp, prob, block_threads=bt, ig_per_thread=k), ref) <= RTOL, (bt, k)
+
+
 def test_benchmark_shape_band_subset(gpp):
     prob = inputs.config("mixed").bands(slice(0, 8))
     assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
