@@ -266,7 +266,8 @@ def measure_batched(torch, gpp, inputs, device):
         if precision == "fp32_bulk":
             for d in dps:
                 d.make_c64()
-        tuned = autotune.tune_batched(dps, precision=precision, proxy_bands=8, reps=1)
+        tuned = autotune.tune_batched(dps, precision=precision, reps=1,
+                                      proxy_fraction=1 / 64 if precision == "fp64" else 1 / 32)
         plan = gpp.BatchedPlan(dps, use_graph=True, precision=precision,
                                block_threads=tuned["block_threads"],
                                ig_per_thread=tuned["ig_per_thread"])

@@ -1,24 +1,25 @@
 """Tile-shape autotuner for the batched GPP launch.
 
 For a batch of instances it times each candidate (threads per CTA, G-vectors per thread
-per tile) on a proxy of the batch -- the same instances truncated to their first
-``proxy_bands`` bands, which keeps every tile count and the shape of the tail while
-shortening each tile -- and keeps the fastest. Results are cached in a JSON file
-(``$GPP_TUNE_CACHE``, default ``~/.cache/gpp/tune.json``) keyed by device, precision, nw
-and the batch's shapes.
+per tile) on a proxy of the batch -- the same instances restricted to a fraction of their
+igp columns (at least one), which keeps every tile's work (all bands x the tile's
+G-vectors) and shortens the batch -- and keeps the fastest. Results are cached in a JSON
+file (``$GPP_TUNE_CACHE``, default ``~/.cache/gpp/tune.json``) keyed by device, precision,
+nw and the batch's shapes.
 """
 
 from __future__ import annotations
 
 import hashlib
 import json
+import math
 import os
 
 import torch
 
 from . import gpp
 
-CANDIDATES = tuple((bt, k) for bt in (64, 128, 256) for k in (1, 2, 4))
+CANDIDATES = tuple((bt, k) for bt in (64, 128, 256) for k in (1, 2, 4, 8))
 
 
 def cache_path() -> str:
@@ -33,11 +34,12 @@ def batch_key(dps, precision: str, occ_mode: str) -> str:
     return f"{dev}|{precision}|{occ_mode}|nw{dps[0].nw}|n{len(dps)}|{sig}"
 
 
-def _proxy(d: gpp.DeviceProblem, bands: int) -> gpp.DeviceProblem:
-    b = min(bands, d.number_bands)
-    return gpp.DeviceProblem(b, d.nvband, d.ncouls, d.ngpown, d.nw, d.aqsmtemp[:b], d.aqsntemp[:b],
-                             d.I_eps_array, d.wtilde_array, d.vcoul, d.inv_igp_index, d.indinv,
-                             d.wx_array[:b], None if d.aqsntemp_c64 is None else d.aqsntemp_c64[:b])
+def _proxy(d: gpp.DeviceProblem, fraction: float) -> gpp.DeviceProblem:
+    """The first ceil(fraction * ngpown) columns of ``d`` (views)."""
+    p = min(d.ngpown, max(1, math.ceil(d.ngpown * fraction)))
+    return gpp.DeviceProblem(d.number_bands, d.nvband, d.ncouls, p, d.nw, d.aqsmtemp,
+                             d.aqsntemp, d.I_eps_array[:p], d.wtilde_array[:p], d.vcoul,
+                             d.inv_igp_index[:p], d.indinv, d.wx_array, d.aqsntemp_c64)
 
 
 def time_plan(plan: gpp.BatchedPlan, reps: int) -> float:
@@ -55,8 +57,9 @@ def time_plan(plan: gpp.BatchedPlan, reps: int) -> float:
     return best
 
 
-def tune_batched(dps, precision: str = "fp64", occ_mode: str = "all", proxy_bands: int = 8,
-                 reps: int = 2, candidates=CANDIDATES, use_cache: bool = True) -> dict:
+def tune_batched(dps, precision: str = "fp64", occ_mode: str = "all",
+                 proxy_fraction: float = 1.0 / 32, reps: int = 2, candidates=CANDIDATES,
+                 use_cache: bool = True) -> dict:
     """Best ``{"block_threads", "ig_per_thread"}`` for this batch (and the timings)."""
     key = batch_key(dps, precision, occ_mode)
     path = cache_path()
@@ -69,7 +72,7 @@ def tune_batched(dps, precision: str = "fp64", occ_mode: str = "all", proxy_band
             cache = {}
         if key in cache:
             return dict(cache[key], cached=True)
-    proxy = [_proxy(d, proxy_bands) for d in dps]
+    proxy = [_proxy(d, proxy_fraction) for d in dps]
     timings = {}
     for bt, k in candidates:
         plan = gpp.BatchedPlan(proxy, use_graph=True, precision=precision, occ_mode=occ_mode,

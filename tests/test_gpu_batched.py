@@ -101,9 +101,9 @@ def test_autotuner(gpp, batch, tmp_path, monkeypatch):
     from paper_2008_11326_gb300 import autotune
     monkeypatch.setenv("GPP_TUNE_CACHE", str(tmp_path / "tune.json"))
     dps = device_batch(gpp, batch)
-    r = autotune.tune_batched(dps, proxy_bands=4, reps=1)
+    r = autotune.tune_batched(dps, proxy_fraction=0.25, reps=1)
     assert (r["block_threads"], r["ig_per_thread"]) in autotune.CANDIDATES and not r["cached"]
-    assert autotune.tune_batched(dps, proxy_bands=4, reps=1)["cached"]
+    assert autotune.tune_batched(dps, proxy_fraction=0.25, reps=1)["cached"]
 
 
 def test_rejects_mixed_nw(gpp):
