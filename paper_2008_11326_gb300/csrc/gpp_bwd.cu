@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
         bwd_terms<W, true, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
       else
         bwd_terms<W, false, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
+      // sum_b M w GI and sum_b M I GW: w and I are the thread's constants, applied at the end
       const double2 M = cmul(amv, an);
-      cmac(gI, cmul(M, w), GI);
-      cmac(gw, cmul(M, I), GW);
+      cmac(gI, M, GI);
+      cmac(gw, M, GW);
       const double2 Q = live ? cmul(Iw, GI) : make_double2(0.0, 0.0);
       s_a[ty][tx] = cmul(amv, Q);
       s_r[ty][tx] = cmul(an, Q);
@@ -235,6 +236,8 @@ __global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
     };
     for (int b = 0; b < nocc; ++b) band(b, BoolTag<true>());
     for (int b = nocc; b < B; ++b) band(b, BoolTag<false>());
+    gI = cmul(w, gI);
+    gw = cmul(I, gw);
     if (live) {
       if (grad_w) grad_w[p * G + ig] = make_double2(gw.x, -gw.y);
       if (grad_I) grad_I[p * G + ig] = make_double2(gI.x, -gI.y);

@@ -53,6 +53,17 @@ __device__ __forceinline__ long long dbits(double v) { return __double_as_longlo
 __device__ __forceinline__ bool gt_nonneg(double a, double b) { return dbits(a) > dbits(b); }
 __device__ __forceinline__ bool lt_nonneg(double a, double b) { return dbits(a) < dbits(b); }
 
+// x / 2 on the integer pipe (the FP64 pipe is the FP64 kernel's bottleneck): one off the
+// exponent field. Exact when that field is in [2, 2046]; +-0, subnormal and smallest-normal
+// x give a signed zero (an absolute error below 2^-1022); infinities and NaN pass through.
+__device__ __forceinline__ double half_alu(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  long long h = (e >= 2) ? b - (1LL << 52) : (b & (1LL << 63));
+  h = (e == 0x7ff) ? b : h;
+  return __longlong_as_double(h);
+}
+
 // FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined by one
 // third-order Householder step of Newton's reciprocal iteration,
 //   e = 1 - d*y,   y' = y * (1 + e + e^2),

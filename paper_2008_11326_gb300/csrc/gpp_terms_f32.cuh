@@ -104,13 +104,12 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
       an_next = ldgf2(an_ptr + static_cast<int64_t>(b + 1) * G);
       am_next = ldgf2(am_ptr + b + 1);
     }
-    const float Mr = fmaf(am.x, an.x, -am.y * an.y);
-    const float Mi = fmaf(am.x, an.y, am.y * an.x);
-    const float Kr = fmaf(Mr, q.Iwr, -Mi * q.Iwi);
-    const float Ki = fmaf(Mr, q.Iwi, Mi * q.Iwr);
-    const float K2r = fmaf(Kr, q.wr, -Ki * q.wi);
-    const float K2i = fmaf(Kr, q.wi, Ki * q.wr);
+    // the band sums run on M = am an; band_loop_f32 multiplies them by I w (the same for
+    // every band) when it merges a chunk
+    const float Kr = fmaf(am.x, an.x, -am.y * an.y);
+    const float Ki = fmaf(am.x, an.y, am.y * an.x);
     const float Kwr = -Ki * q.wi, Kwi = Kr * q.wi;
+    const float K2r = fmaf(Kr, q.wr, Kwr), K2i = fmaf(Ki, q.wr, Kwi);
     const float P1r = -K2i * q.w2i, P1i = K2r * q.w2i;
     const BandEntry32* e = bt32 + static_cast<int64_t>(b) * W;
 #pragma unroll
@@ -242,12 +241,15 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
     bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, sp, q, c);
     if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, sp, q, c);
-    // Kahan merge of the chunk sums; the pair holds the running sum as hi + lo
+    // the chunk sums times I w, merged into the pairs with Kahan's compensation (the pair
+    // holds the running sum as hi + lo)
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) {
+      const float cr = c[k & ~1], ci = c[k | 1];
+      const float v = (k & 1) ? fmaf(q.Iwr, ci, q.Iwi * cr) : fmaf(q.Iwr, cr, -q.Iwi * ci);
       float& hi = *F32Slots<W>::pair(sp, k);
       float& lo = *F32Slots<W>::pair(sp, 4 * W + k);
-      const float y = c[k] + lo;
+      const float y = v + lo;
       const float t = hi + y;
       lo = y - (t - hi);
       hi = t;

@@ -12,14 +12,16 @@ namespace gpp {
 // >= 0: branch 1 is exactly |wdiff|^2 > 1/4 and |S|^2 = |A|^2 + 4 x Re(w) has no
 // cancellation. Otherwise the general form evaluates both thresholds and forms S directly.
 //
-// Per band the caller has formed K = M I w, K2 = K w and the cross terms that do not
-// depend on the frequency:
-//   Kw = (-Im K Im w, Re K Im w)     so that K conj(A) = (Re K Ar + Kw.re, Im K Ar + Kw.im)
-//   P1 = (-Im K2 Im w^2, Re K2 Im w^2)  so that K2 conj(C) = (Re K2 Yr + P1.re, Im K2 Yr + P1.im)
-//   P2 = Kw / 2                         so that K (-conj(S)/2) = (Re K Yr + P2.re, Im K Yr + P2.im)
+// Every term is linear in K = M I w, and I w is the same for all bands of the pair, so
+// the band sum runs on M (the weight product) and band_loop multiplies by I w once at the
+// end. Per band the caller has formed M, M2 = M w and the cross terms that do not depend on
+// the frequency:
+//   Mw = (-Im M Im w, Re M Im w)     so that M conj(A) = (Re M Ar + Mw.re, Im M Ar + Mw.im)
+//   P1 = (-Im M2 Im w^2, Re M2 Im w^2)  so that M2 conj(C) = (Re M2 Yr + P1.re, Im M2 Yr + P1.im)
+//   P2 = Mw / 2 (halved on the integer pipe) so that M (-conj(S)/2) = (Re M Yr + P2.re, Im M Yr + P2.im)
 // with Yr = x^2 - Re w^2 (branch 1) or -(x + Re w)/2 (branch 2).
 struct BandK {
-  double Kr, Ki, K2r, K2i, Kwr, Kwi, P1r, P1i, P2r, P2i;
+  double Kr, Ki, K2r, K2i, Kwr, Kwi, P1r, P1i, P2r, P2i;  // M, M2, Mw, P1, P2
 };
 
 template <int W, bool FAST, bool OCC>
@@ -48,10 +50,24 @@ __device__ __forceinline__ void band_terms(const BandK& k,
       c2 = gt_nonneg(wabs2, kTolZero * A2);
     }
     const double r = rcp_refined(A2 * S2);
-    // achtemp, branch 1 only: K conj(A) / |A|^2
-    const double a1 = c1 ? S2 * r : 0.0;
     const double tr = fma(k.Kr, Ar, k.Kwr);
     const double ti = fma(k.Ki, Ar, k.Kwi);
+    if (FAST && __all_sync(0xffffffffu, c1)) {
+      // the whole warp on branch 1: no selects, and the branch-2 coefficient is not formed
+      const double a1 = S2 * r;
+      acc[4 * iw + 0] = fma(tr, a1, acc[4 * iw + 0]);
+      acc[4 * iw + 1] = fma(ti, a1, acc[4 * iw + 1]);
+      if (OCC) {
+        const double Yr = x2 + mw2r;
+        const double ur = fma(k.K2r, Yr, k.P1r);
+        const double ui = fma(k.K2i, Yr, k.P1i);
+        acc[4 * iw + 2] = fma(ur, r, acc[4 * iw + 2]);
+        acc[4 * iw + 3] = fma(ui, r, acc[4 * iw + 3]);
+      }
+      continue;
+    }
+    // achtemp, branch 1 only: K conj(A) / |A|^2
+    const double a1 = c1 ? S2 * r : 0.0;
     acc[4 * iw + 0] = fma(tr, a1, acc[4 * iw + 0]);
     acc[4 * iw + 1] = fma(ti, a1, acc[4 * iw + 1]);
     if (OCC) {
@@ -75,33 +91,30 @@ __device__ __forceinline__ void band_range(int b0, int b1, int64_t G,
                                            const double2* __restrict__ an_ptr,
                                            const double2* __restrict__ am_ptr,
                                            const BandEntry* __restrict__ bt, bool live, double wr,
-                                           double wi, double Iwr, double Iwi, double wi2,
-                                           double wabs2, double mw2r, double w2i, double wrh,
-                                           double wih, double (&acc)[4 * W]) {
+                                           double wi, double wi2, double wabs2, double mw2r,
+                                           double w2i, double wrh, double (&acc)[4 * W]) {
 #pragma unroll 1
   for (int b = b0; b < b1; ++b) {
     const double2 an = live ? ldg2(an_ptr + static_cast<int64_t>(b) * G) : make_double2(0.0, 0.0);
     const double2 am = ldg2(am_ptr + b);
     BandK k;
-    // M = am * an with am = conj(aqsmtemp[b][g]) vcoul[g]; K = M I w; K2 = K w
-    const double Mr = fma(am.x, an.x, -am.y * an.y);
-    const double Mi = fma(am.x, an.y, am.y * an.x);
-    k.Kr = fma(Mr, Iwr, -Mi * Iwi);
-    k.Ki = fma(Mr, Iwi, Mi * Iwr);
-    k.K2r = fma(k.Kr, wr, -k.Ki * wi);
-    k.K2i = fma(k.Kr, wi, k.Ki * wr);
+    // M = am * an with am = conj(aqsmtemp[b][g]) vcoul[g]; M2 = M w
+    k.Kr = fma(am.x, an.x, -am.y * an.y);
+    k.Ki = fma(am.x, an.y, am.y * an.x);
     k.Kwr = -k.Ki * wi;
     k.Kwi = k.Kr * wi;
+    k.K2r = fma(k.Kr, wr, k.Kwr);   // Re M wr - Im M wi
+    k.K2i = fma(k.Ki, wr, k.Kwi);   // Im M wr + Re M wi
     k.P1r = -k.K2i * w2i;
     k.P1i = k.K2r * w2i;
-    k.P2r = -k.Ki * wih;
-    k.P2i = k.Kr * wih;
+    k.P2r = half_alu(k.Kwr);
+    k.P2i = half_alu(k.Kwi);
     band_terms<W, FAST, OCC>(k, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r, wrh, acc);
   }
 }
 
-// All bands of the thread's (p, ig) pair: bands [0, nocc) enter both sums, the rest only
-// achtemp.
+// All bands of the thread's (p, ig) pair, added to acc: bands [0, nocc) enter both sums,
+// the rest only achtemp. The band sums are formed with M and multiplied by Iw = I w here.
 template <int W, bool FAST>
 __device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
                                           const double2* __restrict__ an_ptr,
@@ -114,12 +127,20 @@ __device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
   const double mw2r = -fma(wr, wr, -wi2);   // -Re w^2
   const double w2i = 2.0 * wr * wi;         // Im w^2
   const double wrh = -0.5 * wr;
-  const double wih = 0.5 * wi;
-  band_range<W, FAST, true>(0, nocc, G, an_ptr, am_ptr, bt, live, wr, wi, Iwr, Iwi, wi2, wabs2,
-                            mw2r, w2i, wrh, wih, acc);
+  double t[4 * W];
+#pragma unroll
+  for (int k = 0; k < 4 * W; ++k) t[k] = 0.0;
+  band_range<W, FAST, true>(0, nocc, G, an_ptr, am_ptr, bt, live, wr, wi, wi2, wabs2, mw2r, w2i,
+                            wrh, t);
   if (nocc < B)
-    band_range<W, FAST, false>(nocc, B, G, an_ptr, am_ptr, bt, live, wr, wi, Iwr, Iwi, wi2, wabs2,
-                               mw2r, w2i, wrh, wih, acc);
+    band_range<W, FAST, false>(nocc, B, G, an_ptr, am_ptr, bt, live, wr, wi, wi2, wabs2, mw2r,
+                               w2i, wrh, t);
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) {   // acc += Iw t, per complex value
+    const double tr = t[2 * k], ti = t[2 * k + 1];
+    acc[2 * k] = fma(Iwr, tr, fma(-Iwi, ti, acc[2 * k]));
+    acc[2 * k + 1] = fma(Iwr, ti, fma(Iwi, tr, acc[2 * k + 1]));
+  }
 }
 
 }  // namespace gpp
