@@ -133,7 +133,7 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
       const double2 uv = make_double2((x2 + mw2r) * r, w2i * r);  // 1/(x^2 - w^2)
       const double2 wuv = cmul(w, uv);
       const double2 h = csel(c1, wuv, v);
-      const double2 T = c1 ? cmul(wuv, uv) : cmul(v, v);
+      const double2 T = cmul(h, csel(c1, uv, v));   // w (uv)^2 or v^2
       const double2 zero = make_double2(0.0, 0.0);
       const double2 ch = c1 ? __ldg(&e[iw].cs) : (c2 ? __ldg(&e[iw].csh) : zero);
       const double2 cT = c1 ? __ldg(&e[iw].cs2x2) : (c2 ? __ldg(&e[iw].csxh) : zero);
@@ -143,32 +143,36 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
   }
 }
 
-// Fixed shared-memory tree: sums v[ty][tx] over ty (into out_col[tx]) and over tx
-// (into out_row[ty]). 256 threads; s_a / s_r hold the kTY x kTX complex values.
+// Fixed shared-memory trees: sums s_a[ty][tx] over ty (into s_a[0][tx]) and s_r[ty][tx]
+// over tx (into s_r[ty][0]). The 256 threads are numbered L = 32 ty + tx and each level's
+// additions go to the lowest L, so every level but the last two of the row tree runs on
+// whole warps (a partly masked warp costs the FP64 pipe as much as a full one): 32 warp
+// additions per band instead of 94 with one row per warp. The two trees share the
+// barriers.
 __device__ __forceinline__ void tile_reduce(double2 (*s_a)[kTX], double2 (*s_r)[kTX]) {
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  // columns: 8 -> 1 along ty
+  const int L = threadIdx.y * kTX + threadIdx.x;
 #pragma unroll
-  for (int h = kTY / 2; h > 0; h >>= 1) {
-    if (ty < h) {
-      s_a[ty][tx].x += s_a[ty + h][tx].x;
-      s_a[ty][tx].y += s_a[ty + h][tx].y;
+  for (int lev = 0; lev < 5; ++lev) {
+    const int hr = (kTX / 2) >> lev;           // row tree: 16, 8, 4, 2, 1
+    if (L < kTY * hr) {
+      const int row = L / hr, col = L - row * hr;
+      s_r[row][col].x += s_r[row][col + hr].x;
+      s_r[row][col].y += s_r[row][col + hr].y;
     }
-    __syncthreads();
-  }
-  // rows: 32 -> 1 along tx, 8 rows at once
-#pragma unroll
-  for (int h = kTX / 2; h > 0; h >>= 1) {
-    if (tx < h) {
-      s_r[ty][tx].x += s_r[ty][tx + h].x;
-      s_r[ty][tx].y += s_r[ty][tx + h].y;
+    if (lev < 3) {
+      const int hc = (kTY / 2) >> lev;         // column tree: 4, 2, 1
+      if (L < kTX * hc) {
+        const int row = L / kTX, col = L - row * kTX;
+        s_a[row][col].x += s_a[row + hc][col].x;
+        s_a[row][col].y += s_a[row + hc][col].y;
+      }
     }
     __syncthreads();
   }
 }
 
 template <int W>
-__global__ void __launch_bounds__(kTX * kTY) gpp_bwd_kernel(
+__global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
     int B, int64_t G, int64_t P, int nocc, int64_t group0, int ngroups, int64_t n_ig_tiles,
     const double2* __restrict__ aqsn, const double2* __restrict__ eps,
     const double2* __restrict__ wt, const double2* __restrict__ am,
