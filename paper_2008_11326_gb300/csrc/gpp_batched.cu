@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
       const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
       if (F32) {
         if (fast) {
-          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
+          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bh32,
+                           d.bt,
                            w, I, live, s_pair);
         } else {  // the general path in FP64, folded into the pairs
           double a[4 * W];

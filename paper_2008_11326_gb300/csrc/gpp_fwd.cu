@@ -60,6 +60,7 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
                                 const int32_t* __restrict__ indinv,
                                 const double* __restrict__ wx, int* flags, int* colg,
                                 BandEntry* bt, double2* am, BandEntry32* bt32, float2* am32,
+                                float2* bh32,
                                 BatchInst* desc_out, const BatchInst desc) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -91,6 +92,16 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
       bt32[i] = e;
     }
   }
+  if (bh32) {  // per band: the frequencies' range, rounded outwards
+    for (int64_t b = tid; b < B; b += stride) {
+      float lo = __int_as_float(0x7f800000), hi = -lo;
+      for (int iw = 0; iw < W; ++iw) {
+        lo = fminf(lo, __double2float_rd(wx[b * W + iw]));
+        hi = fmaxf(hi, __double2float_ru(wx[b * W + iw]));
+      }
+      bh32[b] = make_float2(lo, hi);
+    }
+  }
 }
 
 }  // namespace
@@ -111,6 +122,7 @@ cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, boo
       reinterpret_cast<BandEntry*>(ws + plan.off_bt), reinterpret_cast<double2*>(ws + plan.off_am),
       fp32 ? reinterpret_cast<BandEntry32*>(ws + plan.off_bt32) : nullptr,
       fp32 ? reinterpret_cast<float2*>(ws + plan.off_am32) : nullptr,
+      fp32 ? reinterpret_cast<float2*>(ws + plan.off_bh32) : nullptr,
       desc ? reinterpret_cast<BatchInst*>(ws + plan.off_desc) : nullptr, desc ? *desc : BatchInst());
   return cudaGetLastError();
 }

@@ -31,7 +31,9 @@
 // |wdiff|^2 near 1/4 for |x| < 1e4), whatever FP32 gives. The kernel forms that interval
 // once per (igp, ig) pair with directed rounding and tests x rounded down and up against it
 // (two comparisons, the same for the whole warp); such terms skip the decision, the
-// margin test, the pole test and both warp votes.
+// margin test, the pole test and both warp votes. When every frequency of a band lies
+// beyond the interval on the same side (a per-band range, rounded outwards, against the
+// interval: one test), the band takes that path for all frequencies at once.
 #pragma once
 
 #include "gpp_device.cuh"
@@ -49,15 +51,12 @@ __device__ __forceinline__ float rcp_approx_f32(float d) {
 
 __device__ __forceinline__ float2 ldgf2(const float2* p) { return __ldg(p); }
 
-// Select on the integer pipe. A plain conditional between two floats can be issued as a
-// floating-point select, which GB300 executes on its (narrow) FP64 pipe; the bitwise
-// selp.b32 keeps it on the integer ALU.
-__device__ __forceinline__ float isel(bool c, float a, float b) {
-  float r;
-  asm("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\tselp.b32 %0, %1, %2, q;\n\t}"
-      : "=f"(r)
-      : "f"(a), "f"(b), "r"(static_cast<int>(c)));
-  return r;
+// Selects on the integer pipe. A plain conditional between two floats can be issued as a
+// floating-point select, which GB300 executes on its (narrow) FP64 pipe; a bitwise blend
+// under an all-ones / all-zeros mask (formed once per term) stays on the integer ALU.
+__device__ __forceinline__ unsigned smask(bool c) { return c ? 0xffffffffu : 0u; }
+__device__ __forceinline__ float msel(unsigned m, float a, float b) {
+  return __uint_as_float((__float_as_uint(a) & m) | (__float_as_uint(b) & ~m));
 }
 
 // Per-(igp, ig) constants of the FP32 path.
@@ -88,7 +87,8 @@ struct F32Slots {
 template <int W, bool OCC>
 __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float2* __restrict__ an_ptr,
                                           const float2* __restrict__ am_ptr,
-                                          const BandEntry32* __restrict__ bt32, float* sp,
+                                          const BandEntry32* __restrict__ bt32,
+                                          const float2* __restrict__ bh32, float* sp,
                                           const PairF32& q, float (&c)[4 * W]) {
   if (b0 >= b1) return;
   // the next band's aqsntemp and weight are loaded one band ahead (their global-memory
@@ -112,6 +112,33 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
     const float K2r = fmaf(Kr, q.wr, Kwr), K2i = fmaf(Ki, q.wr, Kwi);
     const float P1r = -K2i * q.w2i, P1i = K2r * q.w2i;
     const BandEntry32* e = bt32 + static_cast<int64_t>(b) * W;
+    // branch 1 for every lane: K conj(A) / |A|^2 and K2 conj(C) / |C|^2
+    auto branch1 = [&](int iw, float x2, float S2, float r, float tr, float ti) {
+      const float a1 = S2 * r;
+      c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
+      c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+      if (OCC) {
+        const float Yr = x2 + q.mw2r;
+        const float ur = fmaf(K2r, Yr, P1r);
+        const float ui = fmaf(K2i, Yr, P1i);
+        c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
+        c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
+      }
+    };
+    const float2 h = __ldg(&bh32[b]);
+    if (h.x > q.hi || h.y < q.lo) {
+      // every frequency of the band outside the warp's interval on the same side
+#pragma unroll
+      for (int iw = 0; iw < W; ++iw) {
+        const float4 ea = __ldg(&e[iw].a);
+        const float Ar = ea.x - q.wr;
+        const float A2 = fmaf(Ar, Ar, q.wi2);
+        const float S2 = fmaf(ea.z, q.wr, A2);
+        const float r = rcp_approx_f32(A2 * S2);
+        branch1(iw, ea.y, S2, r, fmaf(Kr, Ar, Kwr), fmaf(Ki, Ar, Kwi));
+      }
+      continue;
+    }
 #pragma unroll
     for (int iw = 0; iw < W; ++iw) {
       const float4 ea = __ldg(&e[iw].a);
@@ -123,19 +150,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
       float r = rcp_approx_f32(A2 * S2);
       const float tr = fmaf(Kr, Ar, Kwr);
       const float ti = fmaf(Ki, Ar, Kwi);
-      if (eb.x > q.hi || eb.y < q.lo) {
-        // x outside the warp's interval: branch 1 for every lane, K conj(A) / |A|^2 and
-        // K2 conj(C) / |C|^2
-        const float a1 = S2 * r;
-        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
-        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
-        if (OCC) {
-          const float Yr = x2 + q.mw2r;
-          const float ur = fmaf(K2r, Yr, P1r);
-          const float ui = fmaf(K2i, Yr, P1i);
-          c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
-          c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
-        }
+      if (eb.x > q.hi || eb.y < q.lo) {  // x outside the warp's interval
+        branch1(iw, x2, S2, r, tr, ti);
         continue;
       }
       float b2 = A2 * r;
@@ -161,28 +177,19 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
         }
       }
       if (__all_sync(0xffffffffu, c1)) {
-        // every lane on branch 1
-        const float a1 = S2 * r;
-        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
-        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
-        if (OCC) {
-          const float Yr = x2 + q.mw2r;
-          const float ur = fmaf(K2r, Yr, P1r);
-          const float ui = fmaf(K2i, Yr, P1i);
-          c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
-          c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
-        }
+        branch1(iw, x2, S2, r, tr, ti);
       } else {
-        const float a1 = isel(c1, S2 * r, 0.0f);
+        const unsigned m = smask(c1);
+        const float a1 = msel(m, S2 * r, 0.0f);
         c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
         c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
         if (OCC) {
           // branch 2: K (-conj(S)/2) / |S|^2 = (Re K Yr - Im K Im w/2, Im K Yr + Re K Im w/2) b2
           const float wih = 0.5f * q.wi;
-          const float coef = isel(c1, r, b2);
-          const float Yr = isel(c1, x2, ea.w) + isel(c1, q.mw2r, -0.5f * q.wr);
-          const float ur = fmaf(isel(c1, K2r, Kr), Yr, isel(c1, P1r, -Ki * wih));
-          const float ui = fmaf(isel(c1, K2i, Ki), Yr, isel(c1, P1i, Kr * wih));
+          const float coef = msel(m, r, b2);
+          const float Yr = msel(m, x2, ea.w) + msel(m, q.mw2r, -0.5f * q.wr);
+          const float ur = fmaf(msel(m, K2r, Kr), Yr, msel(m, P1r, -Ki * wih));
+          const float ui = fmaf(msel(m, K2i, Ki), Yr, msel(m, P1i, Kr * wih));
           c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
           c[4 * iw + 3] = fmaf(ui, coef, c[4 * iw + 3]);
         }
@@ -203,6 +210,7 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
                                               const float2* __restrict__ an_ptr,
                                               const float2* __restrict__ am_ptr,
                                               const BandEntry32* __restrict__ bt32,
+                                              const float2* __restrict__ bh32,
                                               const BandEntry* __restrict__ bt64,
                                               double2 w64, double2 I64, bool live,
                                               float* sp) {
@@ -239,8 +247,8 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
     const int bend = min(b0 + kChunk, B);
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
-    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, sp, q, c);
-    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, sp, q, c);
+    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, bh32, sp, q, c);
+    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, bh32, sp, q, c);
     // the chunk sums times I w, merged into the pairs with Kahan's compensation (the pair
     // holds the running sum as hi + lo)
 #pragma unroll
