@@ -378,6 +378,33 @@ def run_gpu(args):
     deterministic = bool(np.array_equal(ach.cpu().numpy(), ref_a) and
                          np.array_equal(asx.cpu().numpy(), ref_s))
 
+    # end to end through the host-array entry point: H2D of every input, sum, D2H (right
+    # after the device-resident steps, on the same GPU state)
+    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True)
+    hws = torch.empty(gpp.host_workspace_size(hp), dtype=torch.uint8, device=device)
+    hout = (torch.empty(prob.nw, dtype=torch.complex128).pin_memory(),
+            torch.empty(prob.nw, dtype=torch.complex128).pin_memory())
+    gpp.sigma_host(hp, workspace=hws, out=hout)
+    e2e_steps = max(1, args.e2e_steps)
+    e2e_stage = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(e2e_steps)]
+    e2e_start = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
+    for evs in e2e_stage:
+        for e in evs:
+            e.record()
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as e2e_clk:
+        s0 = time.perf_counter()
+        for k in range(e2e_steps):
+            e2e_start[k].record()
+            gpp.sigma_host(hp, workspace=hws, out=hout, stage_events=e2e_stage[k])
+        e2e_s = (time.perf_counter() - s0) / e2e_steps
+    e2e_ok = bool(np.array_equal(hout[0].numpy(), ref_a) and np.array_equal(hout[1].numpy(), ref_s))
+    e2e_h2d_ms = statistics.mean(e2e_start[k].elapsed_time(e2e_stage[k][0]) for k in range(e2e_steps))
+    e2e_main_ms = statistics.mean(e2e_stage[k][1].elapsed_time(e2e_stage[k][2])
+                                  for k in range(e2e_steps))
+    del hws, hp
+    torch.cuda.empty_cache()
+
     # FP32-bulk forward on the same instance: speedup over FP64 and error against it
     c0 = torch.cuda.Event(enable_timing=True)
     c1 = torch.cuda.Event(enable_timing=True)
@@ -418,24 +445,6 @@ def run_gpu(args):
                  "fp32_peak_frac_model": flops / (f32_main_ms * 1e-3) / 1e12 / peaks["fp32_tflops"]}
     del ws32
 
-    # end to end through the host-array entry point: H2D of every input, sum, D2H
-    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True)
-    del dp
-    torch.cuda.empty_cache()
-    hws = torch.empty(gpp.host_workspace_size(hp), dtype=torch.uint8, device=device)
-    hout = (torch.empty(prob.nw, dtype=torch.complex128).pin_memory(),
-            torch.empty(prob.nw, dtype=torch.complex128).pin_memory())
-    gpp.sigma_host(hp, workspace=hws, out=hout)
-    e2e_steps = max(1, args.e2e_steps)
-    torch.cuda.synchronize(device)
-    s0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        gpp.sigma_host(hp, workspace=hws, out=hout)
-    e2e_s = (time.perf_counter() - s0) / e2e_steps
-    e2e_ok = bool(np.array_equal(hout[0].numpy(), ref_a) and np.array_equal(hout[1].numpy(), ref_s))
-
-    del hws, hp
-    torch.cuda.empty_cache()
     adjoint = None if args.no_extras else measure_adjoint(torch, gpp, inputs, device)
     batched = None if args.no_extras else measure_batched(torch, gpp, inputs, device)
 
@@ -476,7 +485,9 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": {"value": world * flops / e2e_s / 1e12, "unit": UNIT,
                     "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 2 * prob.nw * 16,
-                    "steps": e2e_steps, "matches_device_result": e2e_ok},
+                    "steps": e2e_steps, "matches_device_result": e2e_ok,
+                    "h2d_ms": e2e_h2d_ms, "main_kernel_ms": e2e_main_ms,
+                    "clocks": e2e_clk.summary()},
             "gpu_launches": 3 * K,
             "deterministic_across_steps": deterministic,
             "clocks": clk.summary(),
