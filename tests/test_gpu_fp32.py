@@ -76,6 +76,21 @@ def test_next_to_the_wdiff_pole(gpp):
     assert rel_err(got, oracle.sigma(prob)) <= RTOL
 
 
+def test_band_frequencies_on_both_sides_of_the_warp_interval(gpp):
+    """Re w in a narrow range, so a band can put one frequency below every Re w of a warp and
+    another above (the per-band range test fails, each frequency is tested alone), next to
+    bands entirely above or below, and bands straddling the interval."""
+    prob = inputs.make_problem(12, 2, 700, 6, 3, seed=81)
+    wt = prob.wtilde_array.copy()
+    wt.real = 1.0 + 0.1 * (wt.real - 0.2) / 2.8
+    wx = np.array([[0.1, 3.0, 0.2], [0.0, 0.3, 2.9], [2.0, 2.5, 4.0], [0.05, 0.1, 0.15],
+                   [1.0, 1.05, 3.0], [0.4, 1.6, 0.45], [5.0, 0.0, 5.0], [1.2, 1.3, 1.4],
+                   [0.2, 0.7, 2.4], [3.3, 0.33, 1.55], [0.0, 0.0, 0.0], [9.0, 8.0, 7.0]])
+    prob = prob.replace(wtilde_array=wt, wx_array=wx)
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+    assert rel_err(run(gpp, prob, precision="fp64"), oracle.sigma(prob)) <= 1e-12
+
+
 def test_general_inputs_take_the_fp64_path(gpp):
     prob = inputs.make_problem(6, 2, 200, 6, 4, seed=77)
     wx = np.linspace(-2.5, 3.5, 24).reshape(6, 4)     # negative x
