@@ -27,8 +27,9 @@ def _terms(w: complex, eps: complex, x: float):
     return 0j, 0j
 
 
-def brute_sigma(prob, occ_mode: int = 0):
-    """(achtemp, asxtemp) as lists of Python complex, one per iw."""
+def brute_sigma(prob, occ_mode: int = 0, ch_half: bool = False, sexcut: float = 0.0):
+    """(achtemp, asxtemp) as lists of Python complex, one per iw. ``ch_half`` halves every
+    sch contribution; ``sexcut > 0`` drops ssx where x < 0 and |ssx| > sexcut |I|."""
     B, V, G, P, W = prob.number_bands, prob.nvband, prob.ncouls, prob.ngpown, prob.nw
     terms_a = [[[], []] for _ in range(W)]
     terms_s = [[[], []] for _ in range(W)]
@@ -45,9 +46,13 @@ def brute_sigma(prob, occ_mode: int = 0):
                 weight = (complex(prob.aqsmtemp[b, g]).conjugate()
                           * complex(prob.aqsntemp[b, ig]) * float(prob.vcoul[g]))
                 for iw in range(W):
-                    sch, ssx = _terms(complex(prob.wtilde_array[p, ig]),
-                                      complex(prob.I_eps_array[p, ig]),
-                                      float(prob.wx_array[b, iw]))
+                    eps = complex(prob.I_eps_array[p, ig])
+                    x = float(prob.wx_array[b, iw])
+                    sch, ssx = _terms(complex(prob.wtilde_array[p, ig]), eps, x)
+                    if sexcut > 0 and x < 0 and abs(ssx) > sexcut * abs(eps):
+                        ssx = 0j
+                    if ch_half:
+                        sch = sch / 2
                     a = weight * sch
                     s = occ * (weight * ssx)
                     terms_a[iw][0].append(a.real)

@@ -59,10 +59,11 @@ class Oracle:
         lib = ctypes.CDLL(path)
         i64, i32, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
         lib.oracle_gpp_sigma.restype = i32
-        lib.oracle_gpp_sigma.argtypes = [i64, i64, i64, i64, i64, i32,
+        dbl = ctypes.c_double
+        lib.oracle_gpp_sigma.argtypes = [i64, i64, i64, i64, i64, i32, i32, dbl,
                                          vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
         lib.oracle_gpp_sigma_adjoint.restype = i32
-        lib.oracle_gpp_sigma_adjoint.argtypes = [i64, i64, i64, i64, i64, i32,
+        lib.oracle_gpp_sigma_adjoint.argtypes = [i64, i64, i64, i64, i64, i32, i32, dbl,
                                                  vp, vp, vp, vp, vp, vp, vp, vp,
                                                  vp, vp, vp, vp, vp, vp, i32]
         lib.oracle_gpp_branch.restype = i32
@@ -87,14 +88,17 @@ class Oracle:
             ptrs.append(p)
         return keep, ptrs
 
-    def sigma(self, prob, occ_mode: int = OCC_ALL, nthreads: int = 0):
-        """Return (achtemp, asxtemp) as complex128 arrays of length nw."""
+    def sigma(self, prob, occ_mode: int = OCC_ALL, nthreads: int = 0, ch_half: bool = False,
+              sexcut: float = 0.0):
+        """Return (achtemp, asxtemp) as complex128 arrays of length nw. ``ch_half`` and
+        ``sexcut`` are the Sigma-code options described in the C source (off by default)."""
         keep, ptrs = self._inputs(prob)
         W = prob.nw
         ach = np.zeros(W, np.complex128)
         asx = np.zeros(W, np.complex128)
         rc = self.lib.oracle_gpp_sigma(prob.number_bands, prob.nvband, prob.ncouls,
-                                       prob.ngpown, W, occ_mode, *ptrs, ach.ctypes.data,
+                                       prob.ngpown, W, occ_mode, int(bool(ch_half)),
+                                       float(sexcut), *ptrs, ach.ctypes.data,
                                        asx.ctypes.data, nthreads)
         if rc != 0:
             raise RuntimeError(f"oracle_gpp_sigma failed with {rc}")
@@ -102,7 +106,8 @@ class Oracle:
         return ach, asx
 
     def sigma_adjoint(self, prob, g_ach, g_asx, occ_mode: int = OCC_ALL, nthreads: int = 0,
-                      want=("wtilde", "I_eps", "aqsm", "aqsn")):
+                      want=("wtilde", "I_eps", "aqsm", "aqsn"), ch_half: bool = False,
+                      sexcut: float = 0.0):
         """Gradients of L with dL = Re(sum conj(g_ach) d ach + conj(g_asx) d asx).
 
         Returns a dict of complex128 arrays (torch convention dL/dRe + i dL/dIm) for the
@@ -115,7 +120,8 @@ class Oracle:
         shapes = {"wtilde": (P, G), "I_eps": (P, G), "aqsm": (B, G), "aqsn": (B, G)}
         out = {k: np.zeros(shapes[k], np.complex128) for k in want}
         ptr = {k: (out[k].ctypes.data if k in out else None) for k in shapes}
-        rc = self.lib.oracle_gpp_sigma_adjoint(B, prob.nvband, G, P, W, occ_mode, *ptrs,
+        rc = self.lib.oracle_gpp_sigma_adjoint(B, prob.nvband, G, P, W, occ_mode,
+                                               int(bool(ch_half)), float(sexcut), *ptrs,
                                                gap, gsp, ptr["wtilde"], ptr["I_eps"],
                                                ptr["aqsm"], ptr["aqsn"], nthreads)
         if rc != 0:
@@ -136,13 +142,16 @@ def default() -> Oracle:
         return _default
 
 
-def sigma(prob, occ_mode: int = OCC_ALL, nthreads: int = 0):
-    return default().sigma(prob, occ_mode, nthreads)
+def sigma(prob, occ_mode: int = OCC_ALL, nthreads: int = 0, ch_half: bool = False,
+          sexcut: float = 0.0):
+    return default().sigma(prob, occ_mode, nthreads, ch_half, sexcut)
 
 
 def sigma_adjoint(prob, g_ach, g_asx, occ_mode: int = OCC_ALL, nthreads: int = 0,
-                  want=("wtilde", "I_eps", "aqsm", "aqsn")):
-    return default().sigma_adjoint(prob, g_ach, g_asx, occ_mode, nthreads, want)
+                  want=("wtilde", "I_eps", "aqsm", "aqsn"), ch_half: bool = False,
+                  sexcut: float = 0.0):
+    return default().sigma_adjoint(prob, g_ach, g_asx, occ_mode, nthreads, want, ch_half,
+                                   sexcut)
 
 
 def branch(w: complex, x: float) -> int:

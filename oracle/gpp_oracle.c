@@ -30,6 +30,12 @@
  * occ(b) = 1 for every band (occ_mode 0, "all bands", as the paper's loop nest sums every
  * band) or [b < nvband] (occ_mode 1, occupied bands only).
  *
+ * Two options from the Sigma code the kernel sits in (BerkeleyGW; not in the paper's loop
+ * nest, off by default):
+ *   ch_half != 0: achtemp[iw] += (1/2) M sch  (the factor 1/2 of the Coulomb-hole sum);
+ *   sexcut > 0:   a term with x < 0 and |ssx| > sexcut |I| takes ssx = 0 (the screened-
+ *                 exchange cutoff; the comparison is strict).
+ *
  * The constants are a reading (the paper does not print their values): LIMITTWO = 0.5^2,
  * LIMITONE = 1 / (4 * 1e-6), TOL_ZERO = 1e-12, all compared against squared moduli with
  * strict inequalities, so a tie falls through to the next branch.
@@ -101,7 +107,12 @@ static inline int64_t global_column(int64_t p, int64_t G, const int32_t *inv_igp
     return g;
 }
 
-/* The plasmon-pole terms for one (w, I, x): returns the branch taken (1, 2 or 3). */
+/* The plasmon-pole terms for one (w, I, x): returns the branch taken (1, 2 or 3). With
+ * sexcut > 0, ssx is set to zero (and *cut to 1, when cut is not NULL) for x < 0 and
+ * |ssx| > sexcut |I|. */
+static int gpp_terms_cut(cplx w, cplx I, double x, double sexcut, cplx *sch, cplx *ssx,
+                         int *cut);
+
 static int gpp_terms(cplx w, cplx I, double x, cplx *sch, cplx *ssx)
 {
     cplx wdiff = x - w;
@@ -124,6 +135,16 @@ static int gpp_terms(cplx w, cplx I, double x, cplx *sch, cplx *ssx)
     return 3;
 }
 
+static int gpp_terms_cut(cplx w, cplx I, double x, double sexcut, cplx *sch, cplx *ssx,
+                         int *cut)
+{
+    int br = gpp_terms(w, I, x, sch, ssx);
+    int c = sexcut > 0.0 && x < 0.0 && cabs(*ssx) > sexcut * cabs(I);
+    if (c) *ssx = 0.0;
+    if (cut) *cut = c;
+    return br;
+}
+
 static int check_sizes(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W)
 {
     if (B < 0 || V < 0 || G < 0 || P < 0 || W < 0) return -2;
@@ -134,9 +155,11 @@ static int check_sizes(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W)
  * Forward sum. All complex arrays are interleaved (re, im) doubles, row-major:
  * aqsmtemp, aqsntemp [B][G]; I_eps_array, wtilde_array [P][G]; vcoul [G];
  * inv_igp_index [P]; indinv [G+1]; wx_array [B][W]. Outputs achtemp, asxtemp [W] complex.
- * nthreads <= 0 uses the OpenMP default. Returns 0, or -2 for negative sizes.
+ * ch_half and sexcut as in the header (0 and 0.0: the paper's sum). nthreads <= 0 uses the
+ * OpenMP default. Returns 0, or -2 for negative sizes.
  */
 int oracle_gpp_sigma(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W, int occ_mode,
+                     int ch_half, double sexcut,
                      const double *aqsmtemp, const double *aqsntemp,
                      const double *I_eps_array, const double *wtilde_array,
                      const double *vcoul, const int32_t *inv_igp_index,
@@ -171,8 +194,8 @@ int oracle_gpp_sigma(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W, int 
                 cplx I = eps[p * G + ig];
                 for (int64_t iw = 0; iw < W; ++iw) {
                     cplx sch, ssx;
-                    gpp_terms(w, I, wx_array[b * W + iw], &sch, &ssx);
-                    cplx a = M * sch;
+                    gpp_terms_cut(w, I, wx_array[b * W + iw], sexcut, &sch, &ssx, NULL);
+                    cplx a = (ch_half ? 0.5 : 1.0) * (M * sch);
                     cplx s = occ * (M * ssx);
                     nsum_add(&acc[2 * iw + 0], creal(a));
                     nsum_add(&acc[2 * iw + 1], cimag(a));
@@ -206,11 +229,13 @@ int oracle_gpp_sigma(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W, int 
  *             d sch/dI = delw                      d ssx/dI = w^2 / (x^2 - w^2)
  *   branch 2: d delw/dw = x / (x - w)^2,  d ssx/d delw = -2 I / (4 delw + 2)^2
  *             d ssx/dw = (d ssx/d delw)(d delw/dw) d ssx/dI = -(w^2) delw / (4 w^2 (delw + 1/2))
+ * and both ssx derivatives are zero where the screened-exchange cutoff sets ssx to zero.
  */
-static void gpp_terms_grad(cplx w, cplx I, double x, cplx *sch, cplx *ssx, cplx *dsch_dw,
-                           cplx *dssx_dw, cplx *dsch_dI, cplx *dssx_dI)
+static void gpp_terms_grad(cplx w, cplx I, double x, double sexcut, cplx *sch, cplx *ssx,
+                           cplx *dsch_dw, cplx *dssx_dw, cplx *dsch_dI, cplx *dssx_dI)
 {
-    int br = gpp_terms(w, I, x, sch, ssx);
+    int cut;
+    int br = gpp_terms_cut(w, I, x, sexcut, sch, ssx, &cut);
     cplx wdiff = x - w;
     if (br == 1) {
         cplx w2 = w * w;
@@ -234,6 +259,10 @@ static void gpp_terms_grad(cplx w, cplx I, double x, cplx *sch, cplx *ssx, cplx 
         *dsch_dI = 0.0;
         *dssx_dI = 0.0;
     }
+    if (cut) { /* ssx is identically zero where the cutoff holds (a locally constant test) */
+        *dssx_dw = 0.0;
+        *dssx_dI = 0.0;
+    }
 }
 
 /*
@@ -248,7 +277,8 @@ static void gpp_terms_grad(cplx w, cplx I, double x, cplx *sch, cplx *ssx, cplx 
  * (aqsntemp, aqsmtemp; entries of aqsmtemp not reached by any column are zero).
  */
 int oracle_gpp_sigma_adjoint(int64_t B, int64_t V, int64_t G, int64_t P, int64_t W,
-                             int occ_mode, const double *aqsmtemp, const double *aqsntemp,
+                             int occ_mode, int ch_half, double sexcut,
+                             const double *aqsmtemp, const double *aqsntemp,
                              const double *I_eps_array, const double *wtilde_array,
                              const double *vcoul, const int32_t *inv_igp_index,
                              const int32_t *indinv, const double *wx_array,
@@ -289,9 +319,9 @@ int oracle_gpp_sigma_adjoint(int64_t B, int64_t V, int64_t G, int64_t P, int64_t
                     cplx M = conj(aqsm[b * G + g]) * aqsn[b * G + ig] * vcoul[g];
                     for (int64_t iw = 0; iw < W; ++iw) {
                         cplx sch, ssx, dsch_dw, dssx_dw, dsch_dI, dssx_dI;
-                        gpp_terms_grad(w, I, wx_array[b * W + iw], &sch, &ssx, &dsch_dw,
-                                       &dssx_dw, &dsch_dI, &dssx_dI);
-                        cplx ca = conj(ga[iw]), cs = conj(gs[iw]);
+                        gpp_terms_grad(w, I, wx_array[b * W + iw], sexcut, &sch, &ssx,
+                                       &dsch_dw, &dssx_dw, &dsch_dI, &dssx_dI);
+                        cplx ca = (ch_half ? 0.5 : 1.0) * conj(ga[iw]), cs = conj(gs[iw]);
                         sum_w += conj(ca * M * dsch_dw + cs * occ * M * dssx_dw);
                         sum_I += conj(ca * M * dsch_dI + cs * occ * M * dssx_dI);
                     }
@@ -323,8 +353,8 @@ int oracle_gpp_sigma_adjoint(int64_t B, int64_t V, int64_t G, int64_t P, int64_t
                     cplx sum_n = 0.0;
                     for (int64_t iw = 0; iw < W; ++iw) {
                         cplx sch, ssx;
-                        gpp_terms(w, I, wx_array[b * W + iw], &sch, &ssx);
-                        cplx ca = conj(ga[iw]), cs = conj(gs[iw]);
+                        gpp_terms_cut(w, I, wx_array[b * W + iw], sexcut, &sch, &ssx, NULL);
+                        cplx ca = (ch_half ? 0.5 : 1.0) * conj(ga[iw]), cs = conj(gs[iw]);
                         /* F = conj(aqsm) aqsn vcoul (sch | occ ssx) */
                         sum_n += conj(ca * m_conj_v * sch + cs * occ * m_conj_v * ssx);
                         sum_m += ca * n_v * sch + cs * occ * n_v * ssx;

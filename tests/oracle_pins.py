@@ -91,6 +91,17 @@ def pin_closed_forms(orc):
     return fails
 
 
+def pin_physics_closed_forms(orc):
+    """The Sigma-code options (half Coulomb-hole factor, screened-exchange cutoff)."""
+    fails = []
+    for case in golden()["physics"]["cases"]:
+        prob = size1_problem(float(Fraction(case["x"])), cfrac(case["w"]))
+        ach, asx = orc.sigma(prob, ch_half=case["ch_half"], sexcut=float(Fraction(case["sexcut"])))
+        if not (_close(ach[0], cfrac(case["ach"])) and _close(asx[0], cfrac(case["asx"]))):
+            fails.append(f"physics closed form {case['name']}: got {ach[0]}, {asx[0]}")
+    return fails
+
+
 def pin_index_case(orc):
     g = golden()["index_case"]
     ach, asx = orc.sigma(index_problem())
@@ -111,6 +122,18 @@ def pin_adjoint_closed_forms(orc):
             for name, want in g[key].items():
                 if not _close(out[name][0, 0], cfrac(want)):
                     fails.append(f"{section} {key} d/d{name}: got {out[name][0, 0]}")
+    return fails
+
+
+def pin_adjoint_physics(orc):
+    g = golden()["adjoint_physics"]
+    prob = size1_problem(-1.1, 1.2)
+    fails = []
+    for key, ga, gs in (("re_ach", 1.0, 0.0), ("im_asx", 0.0, 1j)):
+        out = orc.sigma_adjoint(prob, np.array([ga]), np.array([gs]), ch_half=True, sexcut=4.0)
+        for name, want in g[key].items():
+            if not _close(out[name][0, 0], cfrac(want)):
+                fails.append(f"adjoint_physics {key} d/d{name}: got {out[name][0, 0]}")
     return fails
 
 
@@ -141,6 +164,15 @@ def pin_brute_force(orc):
             err = max(np.abs(ach - np.array(ba)).max(), np.abs(asx - np.array(bs)).max())
             if not err <= 1e-13 * scale:
                 fails.append(f"brute force case {i} occ {occ}: err {err:.3e} scale {scale:.3e}")
+    # the Sigma-code options, on the case with frequencies of both signs
+    prob = brute_problems()[2]
+    for ch_half, sexcut in ((True, 0.0), (False, 1.5), (True, 4.0)):
+        ach, asx = orc.sigma(prob, ch_half=ch_half, sexcut=sexcut)
+        ba, bs = oracle_pkg.brute_sigma(prob, ch_half=ch_half, sexcut=sexcut)
+        scale = max(np.abs(ba).max(), np.abs(bs).max(), 1e-300)
+        err = max(np.abs(ach - np.array(ba)).max(), np.abs(asx - np.array(bs)).max())
+        if not err <= 1e-13 * scale:
+            fails.append(f"brute force options {ch_half} {sexcut}: err {err:.3e}")
     return fails
 
 
@@ -231,22 +263,27 @@ def pin_invariants(orc):
     return fails
 
 
-def _loss(orc, prob, ga, gs):
-    ach, asx = orc.sigma(prob)
+def _loss(orc, prob, ga, gs, **phys):
+    ach, asx = orc.sigma(prob, **phys)
     return float(np.sum(np.real(np.conj(ga) * ach)) + np.sum(np.real(np.conj(gs) * asx)))
 
 
-def _away_from_thresholds(prob, p, ig, margin=0.1):
+def _away_from_thresholds(prob, p, ig, margin=0.1, sexcut=0.0):
     w = prob.wtilde_array[p, ig]
     x = prob.wx_array.reshape(-1)
     wdiffr = np.abs(x - w) ** 2
     delwr = np.abs(w) ** 2 / wdiffr
     ok = (np.abs(wdiffr / LIMITTWO - 1) >= margin) & (np.abs(delwr / LIMITONE - 1) >= margin)
     ok &= np.abs(delwr / TOL_ZERO - 1) >= margin
+    if sexcut > 0:  # |ssx| / |I| away from the cutoff wherever it applies (x < 0)
+        b1 = (wdiffr > LIMITTWO) & (delwr < LIMITONE)
+        ratio = np.where(b1, np.abs(w) ** 2 / np.abs(x * x - w * w),
+                         np.abs(w) / (2 * np.abs(x + w)))
+        ok &= (x >= 0) | (np.abs(ratio / sexcut - 1) >= margin)
     return bool(np.all(ok))
 
 
-def fd_entries(prob, n_per_kind, rng):
+def fd_entries(prob, n_per_kind, rng, sexcut=0.0):
     """(kind, index) pairs; wtilde entries keep every term >= 10% from a threshold."""
     B, G, P = prob.number_bands, prob.ncouls, prob.ngpown
     cols = [int(prob.indinv[k]) for k in prob.inv_igp_index if 0 <= k <= G]
@@ -259,7 +296,7 @@ def fd_entries(prob, n_per_kind, rng):
                 break
             if kind in ("wtilde", "I_eps"):
                 idx = (int(rng.integers(P)), int(rng.integers(G)))
-                if kind == "wtilde" and not _away_from_thresholds(prob, *idx):
+                if kind == "wtilde" and not _away_from_thresholds(prob, *idx, sexcut=sexcut):
                     continue
             elif kind == "aqsm":
                 idx = (int(rng.integers(B)), int(rng.choice(cols)))
@@ -274,7 +311,7 @@ _FIELD = {"wtilde": "wtilde_array", "I_eps": "I_eps_array", "aqsm": "aqsmtemp",
           "aqsn": "aqsntemp"}
 
 
-def central_difference(orc, prob, ga, gs, kind, idx, h=1e-6):
+def central_difference(orc, prob, ga, gs, kind, idx, h=1e-6, **phys):
     field = _FIELD[kind]
     parts = []
     for step in (h, 1j * h):
@@ -282,7 +319,7 @@ def central_difference(orc, prob, ga, gs, kind, idx, h=1e-6):
         for sgn in (1, -1):
             arr = getattr(prob, field).copy()
             arr[idx] += sgn * step
-            vals.append(_loss(orc, prob.replace(**{field: arr}), ga, gs))
+            vals.append(_loss(orc, prob.replace(**{field: arr}), ga, gs, **phys))
         parts.append((vals[0] - vals[1]) / (2 * h))
     return complex(parts[0], parts[1])
 
@@ -307,8 +344,21 @@ def pin_adjoint_fd(orc, n_per_kind=4):
             adj = grads[kind][idx]
             if not abs(fd - adj) <= 1e-6 * max(abs(adj), 1e-2):
                 fails.append(f"adjoint vs FD problem {k} d/d{kind}{idx}: adj {adj} fd {fd}")
+    # the Sigma-code options, on frequencies of both signs (some terms cut, some kept)
+    prob = fd_problems()[1]
+    prob = prob.replace(wx_array=prob.wx_array - 1.6)
+    phys = dict(ch_half=True, sexcut=1.5)
+    ga, gs = inputs.cotangents(4, prob.nw)
+    grads = orc.sigma_adjoint(prob, ga, gs, **phys)
+    rng = np.random.Generator(np.random.PCG64(8))
+    for kind, idx in fd_entries(prob, n_per_kind, rng, sexcut=phys["sexcut"]):
+        fd = central_difference(orc, prob, ga, gs, kind, idx, **phys)
+        adj = grads[kind][idx]
+        if not abs(fd - adj) <= 1e-6 * max(abs(adj), 1e-2):
+            fails.append(f"adjoint vs FD with options d/d{kind}{idx}: adj {adj} fd {fd}")
     return fails
 
 
-ALL_PINS = (pin_closed_forms, pin_index_case, pin_adjoint_closed_forms, pin_brute_force,
-            pin_invariants, pin_adjoint_fd)
+ALL_PINS = (pin_closed_forms, pin_physics_closed_forms, pin_index_case,
+            pin_adjoint_closed_forms, pin_adjoint_physics, pin_brute_force, pin_invariants,
+            pin_adjoint_fd)

@@ -20,8 +20,8 @@ MUTANTS = {
                                  "cplx mgp = conj(aqsm[b * G + p]);"),
     "wtilde transposed": ("cplx w = wt[p * G + ig];\n                cplx I = eps[p * G + ig];\n                for (int64_t iw",
                           "cplx w = wt[ig * P + p];\n                cplx I = eps[p * G + ig];\n                for (int64_t iw"),
-    "wx transposed": ("gpp_terms(w, I, wx_array[b * W + iw], &sch, &ssx);\n                    cplx a",
-                      "gpp_terms(w, I, wx_array[iw * B + b], &sch, &ssx);\n                    cplx a"),
+    "wx transposed": ("gpp_terms_cut(w, I, wx_array[b * W + iw], sexcut, &sch, &ssx, NULL);\n                    cplx a",
+                      "gpp_terms_cut(w, I, wx_array[iw * B + b], sexcut, &sch, &ssx, NULL);\n                    cplx a"),
     "branch-2 sign": ("*ssx = -(w2 * I) * delw / (4.0 * w2 * (delw + 0.5));",
                       "*ssx = (w2 * I) * delw / (4.0 * w2 * (delw + 0.5));"),
     "branch-2 half": ("(4.0 * w2 * (delw + 0.5))", "(4.0 * w2 * (delw + 1.0))"),
@@ -42,6 +42,14 @@ MUTANTS = {
     "adjoint branch-2 chain": ("*dssx_dw = (-2.0 * I / (d4 * d4)) * ddelw_dw;",
                                "*dssx_dw = (-2.0 * I / (d4 * d4));"),
     "adjoint dssx/dI": ("*dssx_dI = w2 / cden;", "*dssx_dI = w / cden;"),
+    "cutoff for any frequency sign": ("sexcut > 0.0 && x < 0.0 && cabs(*ssx)",
+                                      "sexcut > 0.0 && cabs(*ssx)"),
+    "cutoff without its factor": ("cabs(*ssx) > sexcut * cabs(I)", "cabs(*ssx) > cabs(I)"),
+    "cutoff at half its factor": ("cabs(*ssx) > sexcut * cabs(I)", "cabs(*ssx) > 0.5 * sexcut * cabs(I)"),
+    "half factor dropped": ("cplx a = (ch_half ? 0.5 : 1.0) * (M * sch);", "cplx a = M * sch;"),
+    "half factor on asx too": ("cplx s = occ * (M * ssx);", "cplx s = (ch_half ? 0.5 : 1.0) * occ * (M * ssx);"),
+    "adjoint half factor dropped": ("cplx ca = (ch_half ? 0.5 : 1.0) * conj(ga[iw])", "cplx ca = conj(ga[iw])"),
+    "adjoint cut derivative kept": ("    if (cut) { /* ssx", "    if (0) { /* ssx"),
 }
 
 
