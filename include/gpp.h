@@ -75,6 +75,14 @@ typedef enum gpp_occ_mode {
     GPP_OCC_OCCUPIED = 1  /* occ(b) = [b < nvband] */
 } gpp_occ_mode;
 
+/* Options of the Sigma code around the kernel (BerkeleyGW; not part of the paper's loop
+ * nest), bits of gpp_options.physics: */
+typedef enum gpp_physics {
+    GPP_PHYS_CH_HALF = 1,   /* achtemp[iw] = (1/2) sum M sch: the factor 1/2 of the Coulomb hole */
+    GPP_PHYS_SX_CUTOFF = 2  /* a term with x < 0 and |ssx| > sexcut |I| takes ssx = 0 (the
+                               screened-exchange cutoff; sexcut from gpp_options.sexcut) */
+} gpp_physics;
+
 #define GPP_MAX_NW 8
 
 typedef struct gpp_c128 {
@@ -117,14 +125,21 @@ typedef struct gpp_options {
     int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
     int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4), max 8; a tile is
                               one igp column x block_threads * ig_per_thread G-vectors x all bands */
-    int32_t reserved[2];   /* must be 0 */
+    int32_t physics;       /* bit set of gpp_physics: 0 = the paper's sum */
+    int32_t reserved;      /* must be 0 */
     /* NULL, or an array of 4 cudaEvent_t (passed as void*) that the call records on its
      * stream: [0] before the column gather, [1] before the main sum, [2] after it, [3] after
      * the final reduction. For timing the main kernel; the events belong to the caller. */
     void *const *stage_events;
+    double sexcut;         /* with GPP_PHYS_SX_CUTOFF: the cutoff factor (> 0, finite; BerkeleyGW
+                              uses 4); ignored otherwise. The kernels test |w|^2 / |x^2 - w^2| >
+                              sexcut (branch 1) and |w| / (2 |x + w|) > sexcut (branch 2), which
+                              equal |ssx| / |I| there, so a term within rounding of the cutoff can
+                              be decided either way */
 } gpp_options;
 
-/* Fills *opt with the defaults (GPP_FP64, GPP_OCC_ALL, default tiles, no debug checks). */
+/* Fills *opt with the defaults (GPP_FP64, GPP_OCC_ALL, default tiles, no debug checks, no
+ * physics options). */
 GPP_API void gpp_options_default(gpp_options *opt);
 
 /*

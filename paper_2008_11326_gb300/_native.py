@@ -20,6 +20,7 @@ STATUS = {0: "GPP_OK", -1: "GPP_ERR_NULL_PTR", -2: "GPP_ERR_BAD_SIZE", -3: "GPP_
 GPP_FP64, GPP_FP32_BULK = 0, 1
 GPP_OCC_ALL, GPP_OCC_OCCUPIED = 0, 1
 GPP_MAX_NW = 8
+GPP_PHYS_CH_HALF, GPP_PHYS_SX_CUTOFF = 1, 2
 PEAK_KINDS = {"dfma": 0, "ffma": 1, "dadd": 2, "dmul": 3, "drcp": 4, "drcp_rn": 5,
               "drcp_approx": 6, "fsel": 7, "fsetp": 8, "isel": 9, "f2f": 10}
 PEAK_CHAINS = 8
@@ -46,7 +47,8 @@ class GppGrads(ctypes.Structure):
 class GppOptions(ctypes.Structure):
     _fields_ = [("precision", _i32), ("occ_mode", _i32), ("block_threads", _i32),
                 ("blocks_per_sm", _i32), ("debug_checks", _i32), ("ig_per_thread", _i32),
-                ("reserved", _i32 * 2), ("stage_events", ctypes.POINTER(_vp))]
+                ("physics", _i32), ("reserved", _i32), ("stage_events", ctypes.POINTER(_vp)),
+                ("sexcut", ctypes.c_double)]
 
 
 # (name, restype, argtypes) of every exported function, in header order.
@@ -118,7 +120,8 @@ def check(rc: int):
 
 
 def options(precision=GPP_FP64, occ_mode=GPP_OCC_ALL, block_threads=0, blocks_per_sm=0,
-            debug_checks=False, stage_events=None, ig_per_thread=0) -> GppOptions:
+            debug_checks=False, stage_events=None, ig_per_thread=0, ch_half=False,
+            sexcut=0.0) -> GppOptions:
     o = GppOptions()
     lib().gpp_options_default(ctypes.byref(o))
     o.precision = precision
@@ -127,6 +130,8 @@ def options(precision=GPP_FP64, occ_mode=GPP_OCC_ALL, block_threads=0, blocks_pe
     o.blocks_per_sm = blocks_per_sm
     o.debug_checks = 1 if debug_checks else 0
     o.ig_per_thread = ig_per_thread
+    o.physics = (GPP_PHYS_CH_HALF if ch_half else 0) | (GPP_PHYS_SX_CUTOFF if sexcut else 0)
+    o.sexcut = float(sexcut)
     if stage_events is not None:
         arr = (_vp * 4)(*[ctypes.c_void_p(h) for h in stage_events])
         o._events_keepalive = arr

@@ -61,8 +61,11 @@ int check_options(const gpp_options& o) {
     return fail(GPP_ERR_BAD_OPTION, "debug_checks must be 0 or 1");
   if (o.ig_per_thread < 0 || o.ig_per_thread > 8)
     return fail(GPP_ERR_BAD_OPTION, "ig_per_thread %d must be in [0, 8]", o.ig_per_thread);
-  for (int i = 0; i < 2; ++i)
-    if (o.reserved[i] != 0) return fail(GPP_ERR_BAD_OPTION, "reserved option fields must be 0");
+  if (o.physics & ~(GPP_PHYS_CH_HALF | GPP_PHYS_SX_CUTOFF))
+    return fail(GPP_ERR_BAD_OPTION, "physics %d has unknown bits", o.physics);
+  if ((o.physics & GPP_PHYS_SX_CUTOFF) && !(o.sexcut > 0.0 && o.sexcut < 1e300))
+    return fail(GPP_ERR_BAD_OPTION, "sexcut %g must be positive and finite", o.sexcut);
+  if (o.reserved != 0) return fail(GPP_ERR_BAD_OPTION, "the reserved option field must be 0");
   return GPP_OK;
 }
 
@@ -166,8 +169,15 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
 }
 
 // The descriptor of a single instance whose gather segments start at `ws`.
-gpp::BatchInst describe(const gpp_problem& p, int occ_mode, bool f32, const gpp::FwdPlan& pl,
-                        char* ws) {
+// The scale of achtemp and the squared cutoff factor the kernels apply (gpp_physics).
+double ach_scale(const gpp_options& o) { return (o.physics & GPP_PHYS_CH_HALF) ? 0.5 : 1.0; }
+double sexcut2(const gpp_options& o) {
+  return (o.physics & GPP_PHYS_SX_CUTOFF) ? o.sexcut * o.sexcut : 0.0;
+}
+
+gpp::BatchInst describe(const gpp_problem& p, const gpp_options& o, bool f32,
+                        const gpp::FwdPlan& pl, char* ws) {
+  const int occ_mode = o.occ_mode;
   gpp::BatchInst d;
   d.B = static_cast<int>(p.number_bands);
   d.nocc = static_cast<int>(occ_mode == GPP_OCC_OCCUPIED ? std::min(p.nvband, p.number_bands)
@@ -188,6 +198,8 @@ gpp::BatchInst describe(const gpp_problem& p, int occ_mode, bool f32, const gpp:
   d.flags = reinterpret_cast<const int*>(ws + pl.off_flags);
   d.ach = p.achtemp;
   d.asx = p.asxtemp;
+  d.ach_scale = ach_scale(o);
+  d.sx2 = sexcut2(o);
   return d;
 }
 
@@ -297,7 +309,7 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
     for (int i = 0; i < 4; ++i) ev[i] = static_cast<cudaEvent_t>(o.stage_events[i]);
   auto mark = [&](int i) -> cudaError_t { return ev[i] ? cudaEventRecord(ev[i], s) : cudaSuccess; };
   const bool f32 = o.precision == GPP_FP32_BULK;
-  gpp::BatchInst desc = describe(p, o.occ_mode, f32, plan, ws);
+  gpp::BatchInst desc = describe(p, o, f32, plan, ws);
   desc.tile0 = 0;
   desc.tile_end = plan.ntiles;
   cudaError_t e = mark(0);
@@ -387,7 +399,8 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
       return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
                   flags[1]);
   }
-  e = gpp::launch_bwd(p, o.occ_mode, plan, ws, grad_achtemp, grad_asxtemp, *grads, s);
+  e = gpp::launch_bwd(p, o.occ_mode, ach_scale(o), sexcut2(o), plan, ws, grad_achtemp,
+                      grad_asxtemp, *grads, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernels");
   g_last_error.clear();
   return GPP_OK;
@@ -399,6 +412,7 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
 struct gpp_batched_plan {
   int n = 0, nw = 0, threads = 128, igpt = 1, grid = 1;
   bool f32 = false;
+  gpp_options opt;  // the validated options (shared by every instance)
   int64_t ntiles = 0;
   char* ws = nullptr;
   size_t total = 0, off_inst = 0, off_counter = 0, off_partials = 0;
@@ -418,6 +432,7 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   gpp_options o;
   int rc = validate(&probs[0], opt, &o);
   if (rc) return rc;
+  bp->opt = o;
   bp->n = n;
   bp->nw = static_cast<int>(probs[0].nw);
   bp->f32 = o.precision == GPP_FP32_BULK;
@@ -486,7 +501,7 @@ int batched_bind(gpp_batched_plan* bp, void* workspace, size_t bytes) {
     const int i = d.index;
     gpp::FwdPlan pl = bp->iplan[i];
     pl.n_ig_tiles = d.n_ig_tiles;
-    gpp::BatchInst full = describe(bp->probs[i], d.occ_mode, bp->f32, pl, bp->ws + bp->ioff[i]);
+    gpp::BatchInst full = describe(bp->probs[i], bp->opt, bp->f32, pl, bp->ws + bp->ioff[i]);
     full.index = i;
     full.tile0 = d.tile0;
     full.tile_end = d.tile_end;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
           const double Iwr = fma(I.x, w.x, -I.y * w.y);
           const double Iwi = fma(I.x, w.y, I.y * w.x);
           band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                              w.x, w.y, Iwr, Iwi, a);
+                              w.x, w.y, Iwr, Iwi, d.sx2, a);
 #pragma unroll
           for (int k = 0; k < 4 * W; ++k) {
             const float h = static_cast<float>(a[k]);
@@ -110,10 +110,10 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
         const double Iwi = fma(I.x, w.y, I.y * w.x);
         if (fast)
           band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                             w.x, w.y, Iwr, Iwi, acc);
+                             w.x, w.y, Iwr, Iwi, 0.0, acc);
         else
           band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                              w.x, w.y, Iwr, Iwi, acc);
+                              w.x, w.y, Iwr, Iwi, d.sx2, acc);
       }
     }
     if (F32) {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) gpp_batched_reduce_kernel(const BatchInst
     if (threadIdx.x == 0) {
       const int iw = k / 4, c = k % 4;
       if (c < 2)
-        reinterpret_cast<double*>(d.ach)[2 * iw + c] = s[0];
+        reinterpret_cast<double*>(d.ach)[2 * iw + c] = s[0] * d.ach_scale;
       else
         reinterpret_cast<double*>(d.asx)[2 * iw + c - 2] = s[0];
     }

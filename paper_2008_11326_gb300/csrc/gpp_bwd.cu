@@ -64,16 +64,19 @@ struct BoolTag {
   static constexpr bool value = V;
 };
 
+// ach_scale: 1/2 with the half Coulomb-hole factor (it scales every achtemp cotangent).
 __global__ void gpp_bwd_prep_kernel(int64_t B, int W, const double* __restrict__ wx,
                                     const double2* __restrict__ g_ach,
-                                    const double2* __restrict__ g_asx, BwdBand* bt) {
+                                    const double2* __restrict__ g_asx, double ach_scale,
+                                    BwdBand* bt) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < B * W;
        i += stride) {
     const int iw = static_cast<int>(i % W);
     const double x = wx[i];
     const double2 ga = g_ach[iw], gs = g_asx[iw];
-    const double2 ca = make_double2(ga.x, -ga.y), cs = make_double2(gs.x, -gs.y);
+    const double2 ca = make_double2(ach_scale * ga.x, -ach_scale * ga.y);
+    const double2 cs = make_double2(gs.x, -gs.y);
     BwdBand e;
     e.lo = make_double2(x, x * x);
     e.hi = make_double2(4.0 * x, 0.0);
@@ -87,11 +90,14 @@ __global__ void gpp_bwd_prep_kernel(int64_t B, int W, const double* __restrict__
   }
 }
 
-// Per-term work for one band, all frequencies: accumulates GI and GW.
+// Per-term work for one band, all frequencies: accumulates GI and GW. sx2 (general form
+// only): sexcut^2 of the screened-exchange cutoff, 0 = off; where it drops ssx (x < 0 and
+// |ssx| / |I| > sexcut, tested as in the forward) the ssx derivatives are zero.
 template <int W, bool FAST, bool OCC>
 __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double wr,
                                           double wi, double wi2, double wabs2, double mw2r,
-                                          double w2i, double2 w, double2& GI, double2& GW) {
+                                          double w2i, double2 w, double sx2, double2& GI,
+                                          double2& GW) {
 #pragma unroll
   for (int iw = 0; iw < W; ++iw) {
     const double2 lo = __ldg(&e[iw].lo);
@@ -110,7 +116,7 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
       c2 = gt_nonneg(wabs2, kTolZero * A2);
     }
     const double r = rcp_refined(A2 * S2);
-    if (__all_sync(0xffffffffu, c1)) {
+    if (FAST && __all_sync(0xffffffffu, c1)) {
       // every lane on branch 1: u = 1/(x - w), uv = 1/(x^2 - w^2)
       const double2 u = make_double2(Ar * (S2 * r), wi * (S2 * r));
       cmac(GI, __ldg(&e[iw].ca), u);
@@ -135,8 +141,12 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
       const double2 h = csel(c1, wuv, v);
       const double2 T = cmul(h, csel(c1, uv, v));   // w (uv)^2 or v^2
       const double2 zero = make_double2(0.0, 0.0);
-      const double2 ch = c1 ? __ldg(&e[iw].cs) : (c2 ? __ldg(&e[iw].csh) : zero);
-      const double2 cT = c1 ? __ldg(&e[iw].cs2x2) : (c2 ? __ldg(&e[iw].csxh) : zero);
+      bool keep = true;
+      if (!FAST)
+        keep = !(sx2 > 0.0 && x < 0.0 &&
+                 (c1 ? gt_nonneg(wabs2 * wabs2 * r, sx2) : gt_nonneg(wabs2, 4.0 * sx2 * S2)));
+      const double2 ch = !keep ? zero : c1 ? __ldg(&e[iw].cs) : (c2 ? __ldg(&e[iw].csh) : zero);
+      const double2 cT = !keep ? zero : c1 ? __ldg(&e[iw].cs2x2) : (c2 ? __ldg(&e[iw].csxh) : zero);
       cmac(GI, ch, h);
       cmac(GW, cT, T);
     }
@@ -179,7 +189,8 @@ __global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
     const BwdBand* __restrict__ bt, const int* __restrict__ colg, const int* __restrict__ flags,
     double2* __restrict__ grad_w, double2* __restrict__ grad_I,
     double2* __restrict__ part_n,  // [ngroups][B][G]
-    double2* __restrict__ part_r)  // [n_ig_tiles][B][ngroups * kTY]
+    double2* __restrict__ part_r,  // [n_ig_tiles][B][ngroups * kTY]
+    double sx2)                    // screened-exchange cutoff, sexcut^2 (0 = off)
 {
   __shared__ double2 s_a[kTY][kTX];
   __shared__ double2 s_r[kTY][kTX];
@@ -220,9 +231,9 @@ __global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
       double2 GI = make_double2(0.0, 0.0), GW = make_double2(0.0, 0.0);
       const BwdBand* e = bt + static_cast<int64_t>(b) * W;
       if (fast)
-        bwd_terms<W, true, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
+        bwd_terms<W, true, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, 0.0, GI, GW);
       else
-        bwd_terms<W, false, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, GI, GW);
+        bwd_terms<W, false, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, sx2, GI, GW);
       // sum_b M w GI and sum_b M I GW: w and I are the thread's constants, applied at the end
       const double2 M = cmul(amv, an);
       cmac(gI, M, GI);
@@ -370,9 +381,9 @@ int64_t bwd_groups(int64_t P) { return (P + kTY - 1) / kTY; }
 int bwd_tile_ig() { return kTX; }
 int bwd_tile_cols() { return kTY; }
 
-cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, char* ws,
-                       const gpp_c128* g_ach, const gpp_c128* g_asx, const gpp_grads& out,
-                       cudaStream_t s) {
+cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, double ach_scale, double sx2,
+                       const BwdPlan& plan, char* ws, const gpp_c128* g_ach,
+                       const gpp_c128* g_asx, const gpp_grads& out, cudaStream_t s) {
   const int64_t B = p.number_bands, G = p.ncouls, P = p.ngpown;
   const int W = static_cast<int>(p.nw);
   int64_t nocc = B;
@@ -380,7 +391,8 @@ cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, 
   BwdBand* bt = reinterpret_cast<BwdBand*>(ws + plan.off_bwd_bt);
   gpp_bwd_prep_kernel<<<grid_for(B * W), 256, 0, s>>>(B, W, p.wx_array,
                                                       reinterpret_cast<const double2*>(g_ach),
-                                                      reinterpret_cast<const double2*>(g_asx), bt);
+                                                      reinterpret_cast<const double2*>(g_asx),
+                                                      ach_scale, bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const double2* am = reinterpret_cast<const double2*>(ws + plan.fwd.off_am);
@@ -403,7 +415,7 @@ cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, 
       reinterpret_cast<const double2*>(p.aqsntemp), reinterpret_cast<const double2*>(p.I_eps_array), \
       reinterpret_cast<const double2*>(p.wtilde_array), am, bt, colg, flags,                      \
       reinterpret_cast<double2*>(out.wtilde_array), reinterpret_cast<double2*>(out.I_eps_array),  \
-      part_n, part_r)
+      part_n, part_r, sx2)
     switch (W) {
       case 1: GPP_BWD_LAUNCH(1); break;
       case 2: GPP_BWD_LAUNCH(2); break;

@@ -61,9 +61,9 @@ int bwd_blocks_per_sm(int nw);
 int64_t bwd_groups(int64_t P);
 int bwd_tile_ig();
 int bwd_tile_cols();
-cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, const BwdPlan& plan, char* ws,
-                       const gpp_c128* g_ach, const gpp_c128* g_asx, const gpp_grads& out,
-                       cudaStream_t s);
+cudaError_t launch_bwd(const gpp_problem& p, int occ_mode, double ach_scale, double sx2,
+                       const BwdPlan& plan, char* ws, const gpp_c128* g_ach,
+                       const gpp_c128* g_asx, const gpp_grads& out, cudaStream_t s);
 
 // One instance of a batched launch (device-resident descriptor; see gpp_batched.cu).
 struct BatchInst {
@@ -84,6 +84,8 @@ struct BatchInst {
   const int* flags = nullptr;
   gpp_c128* ach = nullptr;
   gpp_c128* asx = nullptr;
+  double ach_scale = 1.0;  // 1/2 with GPP_PHYS_CH_HALF
+  double sx2 = 0.0;        // sexcut^2 with GPP_PHYS_SX_CUTOFF, else 0
 };
 
 // Lets the main kernel take the shared memory the launch shape needs; before occupancy

@@ -24,11 +24,15 @@ struct BandK {
   double Kr, Ki, K2r, K2i, Kwr, Kwi, P1r, P1i, P2r, P2i;  // M, M2, Mw, P1, P2
 };
 
+// sx2 (general form only): sexcut^2 of the screened-exchange cutoff, 0 = off. The cutoff
+// drops ssx where x < 0 and |ssx| > sexcut |I|; |ssx| / |I| is |w|^2 / |C| on branch 1 and
+// |w| / (2 |S|) on branch 2, compared as |w|^4 / |C|^2 > sx2 and |w|^2 > 4 sx2 |S|^2. (The
+// fast path has x >= 0, where the cutoff never applies.)
 template <int W, bool FAST, bool OCC>
 __device__ __forceinline__ void band_terms(const BandK& k,
                                            const BandEntry* __restrict__ btb, double wr,
                                            double wi2, double wabs2, double mw2r, double wrh,
-                                           double (&acc)[4 * W]) {
+                                           double sx2, double (&acc)[4 * W]) {
 #pragma unroll
   for (int iw = 0; iw < W; ++iw) {
     const double2 xlo = __ldg(&btb[iw].lo);
@@ -73,7 +77,13 @@ __device__ __forceinline__ void band_terms(const BandK& k,
     if (OCC) {
       // asxtemp: branch 1 -> K2 conj(C) / |C|^2,  branch 2 -> K (-conj(S)/2) / |S|^2
       const double b2 = A2 * r;
-      const double coef = c1 ? r : (c2 ? b2 : 0.0);
+      double coef = c1 ? r : (c2 ? b2 : 0.0);
+      if (!FAST) {
+        const bool cut = sx2 > 0.0 && x < 0.0 &&
+                         (c1 ? gt_nonneg(wabs2 * wabs2 * r, sx2)
+                             : gt_nonneg(wabs2, 4.0 * sx2 * S2));
+        coef = cut ? 0.0 : coef;
+      }
       const double Yr = (c1 ? x2 : xh) + (c1 ? mw2r : wrh);
       const double ur = fma(c1 ? k.K2r : k.Kr, Yr, c1 ? k.P1r : k.P2r);
       const double ui = fma(c1 ? k.K2i : k.Ki, Yr, c1 ? k.P1i : k.P2i);
@@ -92,7 +102,8 @@ __device__ __forceinline__ void band_range(int b0, int b1, int64_t G,
                                            const double2* __restrict__ am_ptr,
                                            const BandEntry* __restrict__ bt, bool live, double wr,
                                            double wi, double wi2, double wabs2, double mw2r,
-                                           double w2i, double wrh, double (&acc)[4 * W]) {
+                                           double w2i, double wrh, double sx2,
+                                           double (&acc)[4 * W]) {
 #pragma unroll 1
   for (int b = b0; b < b1; ++b) {
     const double2 an = live ? ldg2(an_ptr + static_cast<int64_t>(b) * G) : make_double2(0.0, 0.0);
@@ -109,19 +120,21 @@ __device__ __forceinline__ void band_range(int b0, int b1, int64_t G,
     k.P1i = k.K2r * w2i;
     k.P2r = half_alu(k.Kwr);
     k.P2i = half_alu(k.Kwi);
-    band_terms<W, FAST, OCC>(k, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r, wrh, acc);
+    band_terms<W, FAST, OCC>(k, bt + static_cast<int64_t>(b) * W, wr, wi2, wabs2, mw2r, wrh, sx2,
+                             acc);
   }
 }
 
 // All bands of the thread's (p, ig) pair, added to acc: bands [0, nocc) enter both sums,
 // the rest only achtemp. The band sums are formed with M and multiplied by Iw = I w here.
+// sx2: the screened-exchange cutoff (general form only; see band_terms).
 template <int W, bool FAST>
 __device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
                                           const double2* __restrict__ an_ptr,
                                           const double2* __restrict__ am_ptr,
                                           const BandEntry* __restrict__ bt, bool live,
                                           double wr, double wi, double Iwr, double Iwi,
-                                          double (&acc)[4 * W]) {
+                                          double sx2, double (&acc)[4 * W]) {
   const double wi2 = wi * wi;
   const double wabs2 = fma(wr, wr, wi2);
   const double mw2r = -fma(wr, wr, -wi2);   // -Re w^2
@@ -131,10 +144,10 @@ __device__ __forceinline__ void band_loop(int B, int64_t G, int nocc,
 #pragma unroll
   for (int k = 0; k < 4 * W; ++k) t[k] = 0.0;
   band_range<W, FAST, true>(0, nocc, G, an_ptr, am_ptr, bt, live, wr, wi, wi2, wabs2, mw2r, w2i,
-                            wrh, t);
+                            wrh, sx2, t);
   if (nocc < B)
     band_range<W, FAST, false>(nocc, B, G, an_ptr, am_ptr, bt, live, wr, wi, wi2, wabs2, mw2r,
-                               w2i, wrh, t);
+                               w2i, wrh, sx2, t);
 #pragma unroll
   for (int k = 0; k < 2 * W; ++k) {   // acc += Iw t, per complex value
     const double tr = t[2 * k], ti = t[2 * k + 1];

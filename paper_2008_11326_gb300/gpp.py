@@ -91,13 +91,15 @@ def _stream_handle(stream, device):
 
 
 def make_options(precision="fp64", occ_mode="all", block_threads=0, blocks_per_sm=0,
-                 debug_checks=False, stage_events=None, ig_per_thread=0) -> N.GppOptions:
+                 debug_checks=False, stage_events=None, ig_per_thread=0, ch_half=False,
+                 sexcut=0.0) -> N.GppOptions:
     """``stage_events``: four recorded ``torch.cuda.Event(enable_timing=True)`` (or raw
-    cudaEvent_t handles) that the call re-records around its stages (see gpp_options)."""
+    cudaEvent_t handles) that the call re-records around its stages (see gpp_options).
+    ``ch_half`` / ``sexcut`` (> 0 turns the cutoff on): the Sigma-code options."""
     if stage_events is not None:
         stage_events = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in stage_events]
     return N.options(PRECISIONS[precision], OCC_MODES[occ_mode], block_threads, blocks_per_sm,
-                     debug_checks, stage_events, ig_per_thread)
+                     debug_checks, stage_events, ig_per_thread, ch_half, sexcut)
 
 
 def workspace_size(dp: DeviceProblem, **opts) -> int:
@@ -116,7 +118,9 @@ def sigma(dp: DeviceProblem, *, out=None, workspace: torch.Tensor | None = None,
 
     Enqueued on ``stream`` (default: torch's current stream) without synchronising.
     ``opts``: precision ('fp64' | 'fp32_bulk'), occ_mode ('all' | 'occupied'),
-    block_threads, blocks_per_sm, debug_checks.
+    block_threads, blocks_per_sm, debug_checks, ig_per_thread, stage_events, and the
+    Sigma-code options ch_half (achtemp halved) and sexcut (> 0: drop ssx where x < 0 and
+    |ssx| > sexcut |I|).
     """
     dev = dp.device
     if out is None:
@@ -219,19 +223,19 @@ class GppSigma(torch.autograd.Function):
     wtilde_array through libgpp's hand-written FP64 adjoint (terms recomputed in backward).
 
     apply(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index, indinv,
-          wx_array, nvband=0, occ_mode='all')
+          wx_array, nvband=0, occ_mode='all', ch_half=False, sexcut=0.0)
     """
 
     @staticmethod
     def forward(ctx, aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index,
-                indinv, wx_array, nvband=0, occ_mode="all"):
+                indinv, wx_array, nvband=0, occ_mode="all", ch_half=False, sexcut=0.0):
         dp = _problem_from(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index,
                            indinv, wx_array, nvband)
-        ach, asx = sigma(dp, occ_mode=occ_mode)
+        ctx.phys = dict(occ_mode=occ_mode, ch_half=ch_half, sexcut=sexcut)
+        ach, asx = sigma(dp, **ctx.phys)
         ctx.save_for_backward(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul,
                               inv_igp_index, indinv, wx_array)
         ctx.nvband = nvband
-        ctx.occ_mode = occ_mode
         return ach, asx
 
     @staticmethod
@@ -246,10 +250,10 @@ class GppSigma(torch.autograd.Function):
         need = ctx.needs_input_grad
         want = [k for k, n in zip(("aqsm", "aqsn", "I_eps", "wtilde"), need[:4]) if n]
         if not want:
-            return (None,) * 10
-        g = sigma_backward(dp, g_ach, g_asx, want=want, occ_mode=ctx.occ_mode)
+            return (None,) * 12
+        g = sigma_backward(dp, g_ach, g_asx, want=want, **ctx.phys)
         return (g.get("aqsm"), g.get("aqsn"), g.get("I_eps"), g.get("wtilde"),
-                None, None, None, None, None, None)
+                None, None, None, None, None, None, None, None)
 
 
 def _problem_from(aqsmtemp, aqsntemp, I_eps_array, wtilde_array, vcoul, inv_igp_index, indinv,

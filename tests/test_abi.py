@@ -60,9 +60,18 @@ def test_host_side_validation(lib):
     o.block_threads = 100
     assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -8
     lib.gpp_options_default(ctypes.byref(o))
-    o.reserved[1] = 3
+    o.reserved = 3
     assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -8
     lib.gpp_options_default(ctypes.byref(o))
+    o.physics = 4
+    assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -8
+    o.physics = N.GPP_PHYS_SX_CUTOFF      # the cutoff without a positive factor
+    assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -8
+    assert b"sexcut" in lib.gpp_last_error()
+    o.sexcut = float("inf")
+    assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -8
+    lib.gpp_options_default(ctypes.byref(o))
+    assert o.physics == 0 and o.sexcut == 0.0
     # outputs missing
     assert lib.gpp_sigma(ctypes.byref(p), ctypes.byref(o), None, 0, None) == -1
     assert b"achtemp" in lib.gpp_last_error()
