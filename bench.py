@@ -314,6 +314,38 @@ def measure_batched(torch, gpp, inputs, device):
     return out
 
 
+def measure_large(torch, gpp, inputs, device):
+    """Three times the benchmark on every loop (B=1536, P=4915, G=98304, nw=3), drawn on the
+    device: the full FP32-bulk sum, and the FP64 sum on its first 32 bands (the full FP64
+    sum takes over a minute)."""
+    c = inputs.CONFIGS["large"]
+    dp = gpp.DeviceProblem(**inputs.make_device_arrays(**c, device=device))
+    dp.make_c64()
+    B, P, G, W = dp.number_bands, dp.ngpown, dp.ncouls, dp.nw
+    nb = 32
+    sub = gpp.DeviceProblem(nb, dp.nvband, G, P, W, dp.aqsmtemp[:nb], dp.aqsntemp[:nb],
+                            dp.I_eps_array, dp.wtilde_array, dp.vcoul, dp.inv_igp_index,
+                            dp.indinv, dp.wx_array[:nb])
+    out = {"workload": f"B{B}_P{P}_G{G}_nw{W} (inputs drawn on the device)",
+           "input_gb": (2 * B * G + 2 * P * G) * 16 / 1e9}
+    for name, prob, prec in (("fp32_bulk", dp, "fp32_bulk"), ("fp64_first_32_bands", sub, "fp64")):
+        ws = torch.empty(gpp.workspace_size(prob, precision=prec), dtype=torch.uint8,
+                         device=device)
+        gpp.sigma(prob, workspace=ws, precision=prec)
+        e = _events(torch, 2)
+        e[0].record()
+        gpp.sigma(prob, workspace=ws, precision=prec)
+        e[1].record()
+        e[1].synchronize()
+        ms = e[0].elapsed_time(e[1])
+        flops = inputs.model_flops(prob.number_bands, P, G, W)
+        out[name] = {"ms": ms, "tflops_model": flops / (ms * 1e-3) / 1e12}
+        del ws
+    del dp, sub
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -447,6 +479,7 @@ def run_gpu(args):
 
     adjoint = None if args.no_extras else measure_adjoint(torch, gpp, inputs, device)
     batched = None if args.no_extras else measure_batched(torch, gpp, inputs, device)
+    large = None if args.no_extras else measure_large(torch, gpp, inputs, device)
 
     if rank != 0:
         if pg is not None:
@@ -493,7 +526,8 @@ def run_gpu(args):
             "clocks": clk.summary(),
             "fp32_bulk": fp32_bulk,
             "adjoint": adjoint,
-            "batched": batched}
+            "batched": batched,
+            "large": large}
     print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()

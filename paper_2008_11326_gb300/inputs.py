@@ -168,12 +168,15 @@ def cotangents(seed: int, nw: int):
 # Named workloads. "tiny" is small enough for the oracle in seconds; "benchmark" is the
 # paper-shaped benchmark (band O(1000), igp O(1000), ig O(10000), paper §II-A) used for the
 # FP64 throughput number; "mixed" is the same shape for the FP32-bulk path; "adjoint" is the
-# gradient workload.
+# gradient workload; "large" scales every loop by 3.
 CONFIGS = {
     "tiny": dict(number_bands=32, nvband=2, ncouls=512, ngpown=64, nw=3, seed=0),
     "benchmark": dict(number_bands=512, nvband=2, ncouls=32768, ngpown=1638, nw=3, seed=1),
     "mixed": dict(number_bands=512, nvband=2, ncouls=32768, ngpown=1638, nw=3, seed=2),
     "adjoint": dict(number_bands=128, nvband=2, ncouls=8192, ngpown=410, nw=3, seed=3),
+    # three times the benchmark on every loop (the paper's larger system is 3-4x its
+    # smaller one on each, §II-A); drawn on the device with make_device_arrays
+    "large": dict(number_bands=1536, nvband=2, ncouls=98304, ngpown=4915, nw=3, seed=5),
 }
 
 
