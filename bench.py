@@ -72,15 +72,17 @@ def base_config(args, world):
 
 # ----------------------------------------------------------------------------- oracle leg
 
-def oracle_sample(prob, bands: int, nthreads: int):
+def oracle_sample(prob, bands: int, nthreads: int, want_result: bool = False):
     """Time the CPU oracle, as it stands, on the first ``bands`` bands of the instance."""
     import oracle
     from paper_2008_11326_gb300 import inputs
     sub = prob.bands(slice(0, bands))
     t0 = time.perf_counter()
-    oracle.sigma(sub, nthreads=nthreads)
+    res = oracle.sigma(sub, nthreads=nthreads)
     dt = time.perf_counter() - t0
     flops = inputs.model_flops(sub.number_bands, sub.ngpown, sub.ncouls, sub.nw)
+    if want_result:
+        return flops / dt / 1e12, dt, sub, res
     return flops / dt / 1e12, dt
 
 
@@ -502,10 +504,23 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, dt = oracle_sample(prob, ORACLE_SAMPLE_BANDS, cores)
+        v, dt, sub, ref = oracle_sample(prob, ORACLE_SAMPLE_BANDS, cores, want_result=True)
+        v1, dt1 = oracle_sample(prob, 1, 1)
+        ref = np.concatenate(ref)
+        parity = {}
+        sdp = gpp.DeviceProblem.from_host(sub, device=device, c64=True)
+        for prec in ("fp64", "fp32_bulk"):
+            a, s = gpp.sigma(sdp, precision=prec)
+            got = np.concatenate([a.cpu().numpy(), s.cpu().numpy()])
+            parity[prec] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+        del sdp
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {ORACLE_SAMPLE_BANDS} of 512 bands of the benchmark instance "
-                         f"({dt:.1f} s, OpenMP over igp on all host cores)"}
+                         f"({dt:.1f} s, OpenMP over igp on all host cores)",
+               "value_1_core": v1,
+               "sample_1_core": f"first band of the benchmark instance ({dt1:.1f} s, one thread)",
+               "full_instance_s_extrapolated": dt * prob.number_bands / ORACLE_SAMPLE_BANDS,
+               "gpu_max_rel_err_on_sample": parity}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

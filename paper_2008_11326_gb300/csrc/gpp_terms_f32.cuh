@@ -176,9 +176,7 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
           }
         }
       }
-      if (__all_sync(0xffffffffu, c1)) {
-        branch1(iw, x2, S2, r, tr, ti);
-      } else {
+      {  // inside the interval a warp is rarely all on branch 1: no vote, select per lane
         const unsigned m = smask(c1);
         const float a1 = msel(m, S2 * r, 0.0f);
         c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
