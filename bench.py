@@ -142,6 +142,13 @@ class ClockSampler:
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # let nvidia-smi finish starting (its driver initialisation delayed the host-to-device
+        # copies of a timed region that began at the same moment) before the caller times
+        deadline = time.perf_counter() + 5.0
+        while (time.perf_counter() < deadline and self.proc.poll() is None
+               and os.path.getsize(self.file.name) == 0):
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):

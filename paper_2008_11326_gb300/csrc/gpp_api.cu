@@ -144,10 +144,10 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = gpp::batched_prepare(pl.threads, pl.nw, f32);
+    if (e == cudaSuccess) e = gpp::batched_prepare(pl.threads, pl.nw, f32, pl.igpt);
     if (e != cudaSuccess) return cuda_fail(e, "querying the device");
     int bps = o.blocks_per_sm ? o.blocks_per_sm
-                              : gpp::batched_blocks_per_sm(pl.threads, pl.nw, f32);
+                              : gpp::batched_blocks_per_sm(pl.threads, pl.nw, f32, pl.igpt);
     if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for %d threads", pl.threads);
     const int64_t tile_ig = static_cast<int64_t>(pl.threads) * pl.igpt;
     pl.n_ig_tiles = (p.ncouls + tile_ig - 1) / tile_ig;
@@ -441,9 +441,10 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = gpp::batched_prepare(bp->threads, bp->nw, bp->f32);
+  if (e == cudaSuccess) e = gpp::batched_prepare(bp->threads, bp->nw, bp->f32, bp->igpt);
   if (e != cudaSuccess) return cuda_fail(e, "querying the device");
-  int bps = o.blocks_per_sm ? o.blocks_per_sm : gpp::batched_blocks_per_sm(bp->threads, bp->nw, bp->f32);
+  int bps = o.blocks_per_sm ? o.blocks_per_sm
+                            : gpp::batched_blocks_per_sm(bp->threads, bp->nw, bp->f32, bp->igpt);
   if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for the batched kernel");
   bp->grid = sms * bps;
   bp->probs.assign(probs, probs + n);

@@ -22,6 +22,37 @@ namespace gpp {
 
 namespace {
 
+// Smallest power of two >= n (n >= 1).
+__host__ __device__ inline int pow2_ceil(int n) {
+  int k = 1;
+  while (k < n) k <<= 1;
+  return k;
+}
+
+// Sorts key[0, n) ascending and permutes idx with it (n a power of two; every thread of
+// the block takes part). A bitonic network: deterministic for fixed keys, and a
+// permutation of idx whatever the keys (NaN compares false and never swaps).
+__device__ inline void bitonic_sort(float* key, int* idx, int n) {
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const float a = key[i], b = key[l];
+          if ((i & k) == 0 ? a > b : a < b) {
+            key[i] = b;
+            key[l] = a;
+            const int t = idx[i];
+            idx[i] = idx[l];
+            idx[l] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Tile partials: FP64 sums (double) for GPP_FP64; compensated FP32 pairs (float2, hi + lo)
 // for GPP_FP32_BULK, so that its main kernel needs no FP64 arithmetic outside the rare
 // exact-decision and near-pole branches. Both are 8 bytes per value.
@@ -37,11 +68,16 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
                                                           double* __restrict__ partials) {
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
-  // FP32-bulk: the threads' compensated pairs, [2][4W][blockDim.x] floats, and their FP64
-  // wtilde, double2[blockDim.x], and the FP64 band table pointer (dynamic shared memory of
-  // batched_smem_bytes)
+  // FP32-bulk: the threads' compensated pairs, [2][4W][blockDim.x] floats, their FP64
+  // wtilde, double2[blockDim.x], the FP64 band table pointer [blockDim.x], then the tile's
+  // G-vectors sorted by Re w (float keys and int positions, pow2_ceil(blockDim.x * igpt)
+  // each) (dynamic shared memory of batched_smem_bytes)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* const s_pair = reinterpret_cast<float*>(dyn_smem);
+  const int tile_n = blockDim.x * igpt;
+  const int sort_n = F32 ? pow2_ceil(tile_n) : 0;
+  float* const s_key = s_pair + (2 * 4 * W + 6) * blockDim.x;
+  int* const s_pos = reinterpret_cast<int*>(s_key + sort_n);
   for (;;) {
     if (threadIdx.x == 0) s_t = static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
@@ -70,10 +106,29 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
     if (F32) {
 #pragma unroll
       for (int k = 0; k < 2 * 4 * W; ++k) s_pair[k * blockDim.x + threadIdx.x] = 0.0f;
+      // The tile's G-vectors in order of Re w, so that the 32 of a warp (consecutive in
+      // that order) span a narrow range of Re w and most frequencies fall outside it (the
+      // far-from-threshold path); inert positions sort last. The sum does not depend on
+      // which thread takes which G-vector.
+      for (int q = threadIdx.x; q < sort_n; q += blockDim.x) {
+        const int64_t ig = igt * tile_n + q;
+        float key = __int_as_float(0x7f800000);
+        if (q < tile_n && ig < G && col_ok) {
+          key = static_cast<float>(__ldg(&d.wt[p * G + ig].x));
+          key = key == key ? key : 0.0f;  // a NaN must still sort among the live positions
+        }
+        s_key[q] = key;
+        s_pos[q] = q;
+      }
+      __syncthreads();
+      bitonic_sort(s_key, s_pos, sort_n);
     }
     for (int j = 0; j < igpt; ++j) {
-      const int64_t ig = (igt * igpt + j) * blockDim.x + threadIdx.x;
-      const bool live = ig < G && col_ok;
+      // F32: a padding position (>= tile_n, key +inf like an inert one) can sort into the
+      // first tile_n slots; it is inert
+      const int q = F32 ? s_pos[j * blockDim.x + threadIdx.x] : 0;
+      const int64_t ig = F32 ? igt * tile_n + q : (igt * igpt + j) * blockDim.x + threadIdx.x;
+      const bool live = (!F32 || q < tile_n) && ig < G && col_ok;
       double2 w = make_double2(0.5, 1.0);  // inert lane: finite terms, zero weight
       double2 I = make_double2(0.0, 0.0);
       if (live) {
@@ -187,30 +242,31 @@ const void* batched_kernel_ptr(int nw, bool f32) {
 
 }  // namespace
 
-size_t batched_smem_bytes(int threads, int nw, bool f32) {
+size_t batched_smem_bytes(int threads, int nw, bool f32, int igpt) {
   return f32 ? static_cast<size_t>(threads) * (2 * 4 * nw * sizeof(float) + 2 * sizeof(double) +
-                                               sizeof(void*))
+                                               sizeof(void*)) +
+                   static_cast<size_t>(pow2_ceil(threads * igpt)) * (sizeof(float) + sizeof(int))
              : 0;
 }
 
 // A CTA whose static + dynamic shared memory exceeds 48 KB (nw >= 6 at 256 threads) must
 // opt in; the kernel's static part (the reduction buffer) is below 4 KB. Called at plan
 // time, outside any stream capture.
-cudaError_t batched_prepare(int threads, int nw, bool f32) {
+cudaError_t batched_prepare(int threads, int nw, bool f32, int igpt) {
   const void* fn = batched_kernel_ptr(nw, f32);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = batched_smem_bytes(threads, nw, f32);
+  const size_t smem = batched_smem_bytes(threads, nw, f32, igpt);
   if (smem + 4096 <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(smem));
 }
 
-int batched_blocks_per_sm(int threads, int nw, bool f32) {
+int batched_blocks_per_sm(int threads, int nw, bool f32, int igpt) {
   const void* fn = batched_kernel_ptr(nw, f32);
   if (!fn) return 0;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads,
-                                                    batched_smem_bytes(threads, nw, f32)) !=
+                                                    batched_smem_bytes(threads, nw, f32, igpt)) !=
       cudaSuccess)
     return 0;
   return n;
@@ -221,7 +277,7 @@ cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles
                                 unsigned long long* counter, double* partials, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const size_t smem = batched_smem_bytes(threads, nw, f32);
+  const size_t smem = batched_smem_bytes(threads, nw, f32, igpt);
 #define GPP_BATCHED_LAUNCH(WV)                                                                    \
   if (f32)                                                                                        \
     gpp_batched_kernel<WV, true><<<grid, threads, smem, s>>>(inst, ninst, ntiles, igpt, counter,  \

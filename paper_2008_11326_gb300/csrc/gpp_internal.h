@@ -90,8 +90,8 @@ struct BatchInst {
 
 // Lets the main kernel take the shared memory the launch shape needs; before occupancy
 // queries and launches.
-cudaError_t batched_prepare(int threads, int nw, bool f32);
-int batched_blocks_per_sm(int threads, int nw, bool f32);
+cudaError_t batched_prepare(int threads, int nw, bool f32, int igpt);
+int batched_blocks_per_sm(int threads, int nw, bool f32, int igpt);
 // Resets the tile counter and runs the persistent main kernel.
 cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles, int nw,
                                 bool f32, int grid, int threads, int igpt,
