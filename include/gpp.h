@@ -169,9 +169,14 @@ GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_
 
 /*
  * gpp_sigma on HOST arrays: every pointer in `prob` (inputs and outputs) is a host pointer
- * (page-locked memory gives the fastest copies). The inputs are copied into `workspace`
- * (a device buffer of gpp_sigma_host_workspace_size() bytes), the sum runs, the outputs
- * are copied back, and the call returns after `stream` has finished (it synchronises).
+ * (page-locked memory gives the fastest copies and lets them overlap the sum). The inputs
+ * are copied into `workspace` (a device buffer of gpp_sigma_host_workspace_size() bytes),
+ * the sum runs, the outputs are copied back, and the call returns after `stream` has
+ * finished (it synchronises). The copies of aqsntemp, I_eps_array and wtilde_array go in
+ * up to 8 chunks of G-vectors on a copy stream while the sum runs the chunks already
+ * copied, alternating between `stream` and a second stream (the library creates both
+ * streams on a device's first call and keeps them); the result equals gpp_sigma's bit for
+ * bit.
  */
 GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void *workspace,
                    size_t workspace_bytes, void *stream);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -615,12 +616,15 @@ namespace {
 
 struct HostLayout {
   size_t off[12];
+  size_t off_counters;  // one tile counter per pipelined chunk
   size_t sigma_off;
   size_t total;
 };
 
+constexpr int kHostMaxChunks = 8;
+
 // Segment order: aqsm, aqsn, eps, wt, vcoul, inv, indinv, wx, aqsn_c64, (two unused),
-// outputs (ach then asx).
+// outputs (ach then asx), then the chunk counters and gpp_sigma's workspace.
 void host_layout(const gpp_problem& p, int precision, size_t sigma_bytes, HostLayout* L) {
   const size_t B = p.number_bands, G = p.ncouls, P = p.ngpown, W = p.nw;
   const bool f32 = precision == GPP_FP32_BULK;
@@ -631,9 +635,54 @@ void host_layout(const gpp_problem& p, int precision, size_t sigma_bytes, HostLa
     L->off[i] = off;
     off = gpp::align_up(off + sizes[i]);
   }
+  L->off_counters = off;
+  off = gpp::align_up(off + kHostMaxChunks * sizeof(unsigned long long));
   L->sigma_off = off;
   L->total = gpp::align_up(off + sigma_bytes);
 }
+
+// Two streams per device for the host entry point, created on first use and kept for the
+// life of the process: one for the host-to-device copies, one for every other chunk of the
+// main sum (so that a chunk's last wave overlaps the next chunk's first).
+struct HostStreams {
+  cudaStream_t copy = nullptr, compute = nullptr;
+};
+
+std::mutex g_host_streams_mu;
+std::vector<HostStreams> g_host_streams;
+
+cudaError_t host_streams(HostStreams* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_host_streams_mu);
+  if (static_cast<int>(g_host_streams.size()) <= dev) g_host_streams.resize(dev + 1);
+  HostStreams& hs = g_host_streams[dev];
+  if (!hs.copy && (e = cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  if (!hs.compute &&
+      (e = cudaStreamCreateWithFlags(&hs.compute, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  *out = hs;
+  return cudaSuccess;
+}
+
+// Events of one host call, destroyed when it returns.
+struct EventSet {
+  std::vector<cudaEvent_t> ev;
+  cudaError_t make(int n) {
+    ev.assign(n, nullptr);
+    for (auto& x : ev) {
+      cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  ~EventSet() {
+    for (auto x : ev)
+      if (x) cudaEventDestroy(x);
+  }
+};
 
 }  // namespace
 
@@ -662,51 +711,133 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   if (!workspace || !aligned(workspace, gpp::kAlign) || workspace_bytes < L.total)
     return fail(GPP_ERR_WORKSPACE, "host-call workspace must be 256-byte aligned with %zu bytes",
                 L.total);
-  char* ws = static_cast<char*>(workspace);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const size_t B = h.number_bands, G = h.ncouls, P = h.ngpown, W = h.nw;
-  const bool f32 = o.precision == GPP_FP32_BULK;
-  struct {
-    const void* src;
-    size_t bytes;
-    int seg;
-  } copies[] = {{h.aqsmtemp, B * G * 16, 0},
-                {h.aqsntemp, B * G * 16, 1},
-                {h.I_eps_array, P * G * 16, 2},
-                {h.wtilde_array, P * G * 16, 3},
-                {h.vcoul, G * 8, 4},
-                {h.inv_igp_index, P * 4, 5},
-                {h.indinv, (G + 1) * 4, 6},
-                {h.wx_array, B * W * 8, 7},
-                {f32 ? h.aqsntemp_c64 : nullptr, B * G * 8, 8},
-                {nullptr, 0, 9},
-                {nullptr, 0, 10}};
-  gpp_problem d = h;
-  void* dptr[11];
-  for (int i = 0; i < 11; ++i) {
-    dptr[i] = ws + L.off[copies[i].seg];
-    if (!copies[i].src || copies[i].bytes == 0) continue;
-    cudaError_t e = cudaMemcpyAsync(dptr[i], copies[i].src, copies[i].bytes,
-                                    cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "copying inputs to the device");
+  const size_t W = h.nw;
+  if (degenerate(h)) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the stream");
+    memset(h.achtemp, 0, W * sizeof(gpp_c128));
+    memset(h.asxtemp, 0, W * sizeof(gpp_c128));
+    g_last_error.clear();
+    return GPP_OK;
   }
-  d.aqsmtemp = static_cast<const gpp_c128*>(dptr[0]);
-  d.aqsntemp = static_cast<const gpp_c128*>(dptr[1]);
-  d.I_eps_array = static_cast<const gpp_c128*>(dptr[2]);
-  d.wtilde_array = static_cast<const gpp_c128*>(dptr[3]);
-  d.vcoul = static_cast<const double*>(dptr[4]);
-  d.inv_igp_index = static_cast<const int32_t*>(dptr[5]);
-  d.indinv = static_cast<const int32_t*>(dptr[6]);
-  d.wx_array = static_cast<const double*>(dptr[7]);
-  d.aqsntemp_c64 = f32 ? static_cast<const gpp_c64*>(dptr[8]) : nullptr;
+  char* ws = static_cast<char*>(workspace);
+  const size_t B = h.number_bands, G = h.ncouls, P = h.ngpown;
+  const bool f32 = o.precision == GPP_FP32_BULK;
+  gpp_problem d = h;
+  d.aqsmtemp = reinterpret_cast<const gpp_c128*>(ws + L.off[0]);
+  d.aqsntemp = reinterpret_cast<const gpp_c128*>(ws + L.off[1]);
+  d.I_eps_array = reinterpret_cast<const gpp_c128*>(ws + L.off[2]);
+  d.wtilde_array = reinterpret_cast<const gpp_c128*>(ws + L.off[3]);
+  d.vcoul = reinterpret_cast<const double*>(ws + L.off[4]);
+  d.inv_igp_index = reinterpret_cast<const int32_t*>(ws + L.off[5]);
+  d.indinv = reinterpret_cast<const int32_t*>(ws + L.off[6]);
+  d.wx_array = reinterpret_cast<const double*>(ws + L.off[7]);
+  d.aqsntemp_c64 = f32 ? reinterpret_cast<const gpp_c64*>(ws + L.off[8]) : nullptr;
   d.achtemp = reinterpret_cast<gpp_c128*>(ws + L.off[11]);
   d.asxtemp = d.achtemp + W;
-  rc = gpp_sigma(&d, &o, ws + L.sigma_off, L.total - L.sigma_off, stream);
-  if (rc) return rc;
-  cudaError_t e = cudaMemcpyAsync(h.achtemp, d.achtemp, W * 16, cudaMemcpyDeviceToHost, s);
+  char* sws = ws + L.sigma_off;
+
+  // The copies overlap the sum. Tiles run G-vector-tile-major, so the tiles of a range of
+  // G-vector tiles need only those G-vectors of aqsntemp, I_eps and wtilde: the sum runs in
+  // up to kHostMaxChunks such chunks, chunk k starting once its columns are on the device,
+  // on two streams in turn. Every tile writes the partial slot it has in gpp_sigma and one
+  // final reduction sums them in the same order, so the result equals gpp_sigma's bit for bit.
+  const int64_t nigt = plan.n_ig_tiles;
+  const double chunk_bytes = 128.0 * (1 << 20);
+  int K = static_cast<int>(std::min<double>(kHostMaxChunks,
+                                            std::max(1.0, (2.0 * P + B) * G * 16 / chunk_bytes)));
+  K = static_cast<int>(std::min<int64_t>(K, nigt));
+  HostStreams hs;
+  cudaError_t e = host_streams(&hs);
+  EventSet ev;
+  // [0] start, [1] common inputs copied, [2] gather done, [3 .. 3+K) chunk k copied,
+  // [3+K] last chunk on the second stream done
+  if (e == cudaSuccess) e = ev.make(4 + K);
+  if (e != cudaSuccess) return cuda_fail(e, "creating the host path's streams and events");
+  const int64_t tile_ig = static_cast<int64_t>(plan.threads) * plan.igpt;
+  auto h2d = [&](size_t seg, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(ws + L.off[seg], src, bytes, cudaMemcpyHostToDevice, hs.copy);
+  };
+  auto h2d_cols = [&](size_t seg, const void* src, size_t esize, size_t rows, int64_t c0,
+                      int64_t c1) {
+    return cudaMemcpy2DAsync(ws + L.off[seg] + c0 * esize, G * esize,
+                             static_cast<const char*>(src) + c0 * esize, G * esize,
+                             (c1 - c0) * esize, rows, cudaMemcpyHostToDevice, hs.copy);
+  };
+  e = cudaEventRecord(ev.ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.copy, ev.ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.compute, ev.ev[0], 0);
+  if (e == cudaSuccess) e = h2d(0, h.aqsmtemp, B * G * 16);
+  if (e == cudaSuccess) e = h2d(4, h.vcoul, G * 8);
+  if (e == cudaSuccess) e = h2d(5, h.inv_igp_index, P * 4);
+  if (e == cudaSuccess) e = h2d(6, h.indinv, (G + 1) * 4);
+  if (e == cudaSuccess) e = h2d(7, h.wx_array, B * W * 8);
+  if (e == cudaSuccess) e = cudaEventRecord(ev.ev[1], hs.copy);
+  std::vector<int64_t> igt0(K + 1);
+  for (int k = 0; k <= K; ++k) igt0[k] = nigt * k / K;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    const int64_t c0 = igt0[k] * tile_ig, c1 = std::min<int64_t>(igt0[k + 1] * tile_ig, G);
+    e = h2d_cols(1, h.aqsntemp, 16, B, c0, c1);
+    if (e == cudaSuccess && f32) e = h2d_cols(8, h.aqsntemp_c64, 8, B, c0, c1);
+    if (e == cudaSuccess) e = h2d_cols(2, h.I_eps_array, 16, P, c0, c1);
+    if (e == cudaSuccess) e = h2d_cols(3, h.wtilde_array, 16, P, c0, c1);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.ev[3 + k], hs.copy);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "copying inputs to the device");
+
+  cudaEvent_t stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (o.stage_events)
+    for (int i = 0; i < 4; ++i) stage[i] = static_cast<cudaEvent_t>(o.stage_events[i]);
+  auto mark = [&](int i) -> cudaError_t {
+    return stage[i] ? cudaEventRecord(stage[i], s) : cudaSuccess;
+  };
+  gpp::BatchInst desc = describe(d, o, f32, plan, sws);
+  desc.tile0 = 0;
+  desc.tile_end = plan.ntiles;
+  e = cudaStreamWaitEvent(s, ev.ev[1], 0);
+  if (e == cudaSuccess) e = mark(0);
+  if (e == cudaSuccess) e = gpp::launch_prep(d, plan, sws, f32, &desc, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  if (o.debug_checks) {
+    int flags[4];
+    e = cudaMemcpyAsync(flags, sws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
+    if (flags[1] > 0)
+      return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
+                  flags[1]);
+  }
+  e = cudaEventRecord(ev.ev[2], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.compute, ev.ev[2], 0);
+  if (e == cudaSuccess) e = mark(1);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  const gpp::BatchInst* dptr = reinterpret_cast<const gpp::BatchInst*>(sws + plan.off_desc);
+  double* partials = reinterpret_cast<double*>(sws + plan.off_partials);
+  auto* counters = reinterpret_cast<unsigned long long*>(ws + L.off_counters);
+  bool second_used = false;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    cudaStream_t sk = (k & 1) ? hs.compute : s;
+    const int64_t t0 = igt0[k] * static_cast<int64_t>(P), t1 = igt0[k + 1] * static_cast<int64_t>(P);
+    const int grid = static_cast<int>(std::min<int64_t>(plan.grid, t1 - t0));
+    e = cudaStreamWaitEvent(sk, ev.ev[3 + k], 0);
+    if (e == cudaSuccess)
+      e = gpp::launch_batched_main(dptr, 1, t1, plan.nw, f32, grid, plan.threads, plan.igpt,
+                                   counters + k, partials, sk, t0);
+    second_used = second_used || (k & 1);
+  }
+  if (e == cudaSuccess && second_used) {
+    e = cudaEventRecord(ev.ev[3 + K], hs.compute);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.ev[3 + K], 0);
+  }
+  if (e == cudaSuccess) e = mark(2);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the main sum");
+  e = gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s);
+  if (e == cudaSuccess) e = mark(3);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.achtemp, d.achtemp, W * 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h.asxtemp, d.asxtemp, W * 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "copying the outputs back");
+  if (e != cudaSuccess) return cuda_fail(e, "running the sum and copying the outputs back");
   g_last_error.clear();
   return GPP_OK;
 }

@@ -63,7 +63,8 @@ __device__ inline void bitonic_sort(float* key, int* idx, int n) {
 // spills at this budget).
 template <int W, bool F32>
 __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_kernel(const BatchInst* __restrict__ inst,
-                                                          int ninst, int64_t ntiles, int igpt,
+                                                          int ninst, int64_t t_begin,
+                                                          int64_t ntiles, int igpt,
                                                           unsigned long long* counter,
                                                           double* __restrict__ partials) {
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
   float* const s_key = s_pair + (2 * 4 * W + 6) * blockDim.x;
   int* const s_pos = reinterpret_cast<int*>(s_key + sort_n);
   for (;;) {
-    if (threadIdx.x == 0) s_t = static_cast<long long>(atomicAdd(counter, 1ULL));
+    if (threadIdx.x == 0) s_t = t_begin + static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
     const int64_t t = s_t;
     __syncthreads();
@@ -274,17 +275,18 @@ int batched_blocks_per_sm(int threads, int nw, bool f32, int igpt) {
 
 cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles, int nw,
                                 bool f32, int grid, int threads, int igpt,
-                                unsigned long long* counter, double* partials, cudaStream_t s) {
+                                unsigned long long* counter, double* partials, cudaStream_t s,
+                                int64_t t_begin) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const size_t smem = batched_smem_bytes(threads, nw, f32, igpt);
 #define GPP_BATCHED_LAUNCH(WV)                                                                    \
   if (f32)                                                                                        \
-    gpp_batched_kernel<WV, true><<<grid, threads, smem, s>>>(inst, ninst, ntiles, igpt, counter,  \
-                                                             partials);                           \
+    gpp_batched_kernel<WV, true><<<grid, threads, smem, s>>>(inst, ninst, t_begin, ntiles, igpt,  \
+                                                             counter, partials);                  \
   else                                                                                            \
-    gpp_batched_kernel<WV, false><<<grid, threads, 0, s>>>(inst, ninst, ntiles, igpt, counter,    \
-                                                           partials)
+    gpp_batched_kernel<WV, false><<<grid, threads, 0, s>>>(inst, ninst, t_begin, ntiles, igpt,    \
+                                                           counter, partials)
   switch (nw) {
     case 1: GPP_BATCHED_LAUNCH(1); break;
     case 2: GPP_BATCHED_LAUNCH(2); break;

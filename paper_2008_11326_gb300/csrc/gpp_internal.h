@@ -92,10 +92,11 @@ struct BatchInst {
 // queries and launches.
 cudaError_t batched_prepare(int threads, int nw, bool f32, int igpt);
 int batched_blocks_per_sm(int threads, int nw, bool f32, int igpt);
-// Resets the tile counter and runs the persistent main kernel.
+// Resets the tile counter and runs the persistent main kernel over tiles [t_begin, ntiles).
 cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles, int nw,
                                 bool f32, int grid, int threads, int igpt,
-                                unsigned long long* counter, double* partials, cudaStream_t s);
+                                unsigned long long* counter, double* partials, cudaStream_t s,
+                                int64_t t_begin = 0);
 // Per-instance fixed-order sum of the tile partials into the outputs.
 cudaError_t launch_batched_reduce(const BatchInst* inst, int ninst, int nw, bool f32,
                                   const double* partials, cudaStream_t s);

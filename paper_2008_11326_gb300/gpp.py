@@ -63,7 +63,10 @@ class DeviceProblem:
 
     def make_c64(self):
         """The complex64 copy of aqsntemp that precision='fp32_bulk' reads per band."""
-        self.aqsntemp_c64 = self.aqsntemp.to(torch.complex64)
+        c = self.aqsntemp.to(torch.complex64)
+        if c.device.type == "cpu" and self.aqsntemp.is_pinned():
+            c = c.pin_memory()
+        self.aqsntemp_c64 = c
         return self
 
     @property

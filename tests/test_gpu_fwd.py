@@ -173,6 +173,26 @@ def test_host_entry_point_matches_device(gpp):
     assert np.array_equal(ach.numpy(), dev[0]) and np.array_equal(asx.numpy(), dev[1])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_host_entry_point_pipelined_chunks(gpp, precision):
+    """An instance large enough for the host entry to overlap its copies with the sum in
+    several G-vector chunks on two streams: the result equals the device entry point's bit
+    for bit (every tile keeps its partial slot and one reduction sums them in order), also
+    with odd launch shapes and a ragged G."""
+    import torch
+    prob = inputs.make_problem(60, 2, 9001, 1100, 3, seed=8)   # (2P + B) G 16 B = 330 MB
+    dev = gpp.DeviceProblem.from_host(prob, device="cuda", c64=precision == "fp32_bulk")
+    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True,
+                                     c64=precision == "fp32_bulk")
+    for opts in ({}, {"block_threads": 96, "ig_per_thread": 3}):
+        a, s = gpp.sigma(dev, precision=precision, **opts)
+        ws = torch.empty(gpp.host_workspace_size(hp, precision=precision, **opts),
+                         dtype=torch.uint8, device="cuda")
+        ha, hs = gpp.sigma_host(hp, workspace=ws, precision=precision, **opts)
+        assert np.array_equal(ha.numpy(), a.cpu().numpy()), opts
+        assert np.array_equal(hs.numpy(), s.cpu().numpy()), opts
+
+
 def test_reciprocal_accuracy(gpp):
     import torch
     g = torch.Generator().manual_seed(0)
