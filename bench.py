@@ -410,6 +410,7 @@ def run_gpu(args):
     barrier()
     total_ms = t0.elapsed_time(t1)
     main_ms = [stage[k][1].elapsed_time(stage[k][2]) for k in range(K)]
+    step_ms_each = [stage[k][0].elapsed_time(stage[k][3]) for k in range(K)]
     step_ms = total_ms / K
     if pg is not None:
         t = torch.tensor([step_ms], dtype=torch.float64, device=device)
@@ -535,6 +536,8 @@ def run_gpu(args):
             "config": base_config(args, world),
             "fp64_peak_frac": value / world / peaks["fp64_tflops"],
             "main_kernel_ms": statistics.mean(main_ms),
+            "step_ms_median": statistics.median(step_ms_each),
+            "step_ms_spread": [min(step_ms_each), max(step_ms_each)],
             "peaks_measured": peaks,
             "roofline": roofline,
             "cpu_baseline": cpu,
