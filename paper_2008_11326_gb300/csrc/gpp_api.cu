@@ -137,8 +137,6 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
     off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 32);
     pl.off_am32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(float));
-    pl.off_bh32 = off;
-    off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * 2 * sizeof(float));
   }
   pl.gather_total = off;
   if (!gather_only) {
@@ -194,7 +192,6 @@ gpp::BatchInst describe(const gpp_problem& p, const gpp_options& o, bool f32,
   d.am32 = f32 ? reinterpret_cast<const float2*>(ws + pl.off_am32) : nullptr;
   d.bt = reinterpret_cast<const gpp::BandEntry*>(ws + pl.off_bt);
   d.bt32 = f32 ? reinterpret_cast<const gpp::BandEntry32*>(ws + pl.off_bt32) : nullptr;
-  d.bh32 = f32 ? reinterpret_cast<const float2*>(ws + pl.off_bh32) : nullptr;
   d.colg = reinterpret_cast<const int*>(ws + pl.off_colvalid);
   d.flags = reinterpret_cast<const int*>(ws + pl.off_flags);
   d.ach = p.achtemp;

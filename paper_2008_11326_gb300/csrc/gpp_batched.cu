@@ -70,14 +70,15 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
   // FP32-bulk: the threads' compensated pairs, [2][4W][blockDim.x] floats, their FP64
-  // wtilde, double2[blockDim.x], the FP64 band table pointer [blockDim.x], then the tile's
+  // wtilde, double2[blockDim.x], the FP64 band table pointer [blockDim.x], I w as
+  // float2[blockDim.x], then the tile's
   // G-vectors sorted by Re w (float keys and int positions, pow2_ceil(blockDim.x * igpt)
   // each) (dynamic shared memory of batched_smem_bytes)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* const s_pair = reinterpret_cast<float*>(dyn_smem);
   const int tile_n = blockDim.x * igpt;
   const int sort_n = F32 ? pow2_ceil(tile_n) : 0;
-  float* const s_key = s_pair + (2 * 4 * W + 6) * blockDim.x;
+  float* const s_key = s_pair + (2 * 4 * W + 8) * blockDim.x;
   int* const s_pos = reinterpret_cast<int*>(s_key + sort_n);
   for (;;) {
     if (threadIdx.x == 0) s_t = t_begin + static_cast<long long>(atomicAdd(counter, 1ULL));
@@ -142,8 +143,7 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
       const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
       if (F32) {
         if (fast) {
-          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bh32,
-                           d.bt,
+          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
                            w, I, live, s_pair);
         } else {  // the general path in FP64, folded into the pairs
           double a[4 * W];
@@ -245,7 +245,7 @@ const void* batched_kernel_ptr(int nw, bool f32) {
 
 size_t batched_smem_bytes(int threads, int nw, bool f32, int igpt) {
   return f32 ? static_cast<size_t>(threads) * (2 * 4 * nw * sizeof(float) + 2 * sizeof(double) +
-                                               sizeof(void*)) +
+                                               sizeof(void*) + 2 * sizeof(float)) +
                    static_cast<size_t>(pow2_ceil(threads * igpt)) * (sizeof(float) + sizeof(int))
              : 0;
 }

@@ -30,11 +30,11 @@ struct alignas(32) BandEntry {
   double2 hi;  // 4x, -x/2
 };
 
-// The FP32 band table entry: x, x^2, 4x, -x/2 rounded to FP32, and the part of the
-// branch-decision margin that depends on x (see gpp_terms_f32.cuh).
+// The FP32 band table entry: x, x^2, 4x rounded to FP32, x rounded down and up, the
+// branch-decision margin (see gpp_terms_f32.cuh) and the band's frequency range.
 struct alignas(32) BandEntry32 {
-  float4 a;  // x, x^2, 4x, -x/2
-  float4 b;  // x rounded down, x rounded up, margin_x, 0
+  float4 a;  // x, x^2, 4x, min over the band's frequencies of x rounded down
+  float4 b;  // x rounded down, x rounded up, margin_x, max over the band's frequencies of x rounded up
 };
 
 // Flags written by the gather kernel: [0] some wx < 0 or NaN, [1] bad index count,

@@ -60,7 +60,6 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
                                 const int32_t* __restrict__ indinv,
                                 const double* __restrict__ wx, int* flags, int* colg,
                                 BandEntry* bt, double2* am, BandEntry32* bt32, float2* am32,
-                                float2* bh32,
                                 BatchInst* desc_out, const BatchInst desc) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -85,21 +84,17 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
     if (!(fabs(x) < kFp32MaxX)) flags[2] = 1;
     if (bt32) {
       const float xf = static_cast<float>(x);
-      BandEntry32 e;
-      e.a = make_float4(xf, static_cast<float>(x * x), 4.0f * xf, -0.5f * xf);
-      e.b = make_float4(__double2float_rd(x), __double2float_ru(x),
-                        kMarginScale * (fabsf(xf) + kMarginW), 0.0f);
-      bt32[i] = e;
-    }
-  }
-  if (bh32) {  // per band: the frequencies' range, rounded outwards
-    for (int64_t b = tid; b < B; b += stride) {
-      float lo = __int_as_float(0x7f800000), hi = -lo;
-      for (int iw = 0; iw < W; ++iw) {
-        lo = fminf(lo, __double2float_rd(wx[b * W + iw]));
-        hi = fmaxf(hi, __double2float_ru(wx[b * W + iw]));
+      const int64_t b0 = i / W;
+      float lo = __int_as_float(0x7f800000), hi = -lo;  // the band's range, rounded outwards
+      for (int k = 0; k < W; ++k) {
+        lo = fminf(lo, __double2float_rd(wx[b0 * W + k]));
+        hi = fmaxf(hi, __double2float_ru(wx[b0 * W + k]));
       }
-      bh32[b] = make_float2(lo, hi);
+      BandEntry32 e;
+      e.a = make_float4(xf, static_cast<float>(x * x), 4.0f * xf, lo);
+      e.b = make_float4(__double2float_rd(x), __double2float_ru(x),
+                        kMarginScale * (fabsf(xf) + kMarginW), hi);
+      bt32[i] = e;
     }
   }
 }
@@ -122,7 +117,6 @@ cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, boo
       reinterpret_cast<BandEntry*>(ws + plan.off_bt), reinterpret_cast<double2*>(ws + plan.off_am),
       fp32 ? reinterpret_cast<BandEntry32*>(ws + plan.off_bt32) : nullptr,
       fp32 ? reinterpret_cast<float2*>(ws + plan.off_am32) : nullptr,
-      fp32 ? reinterpret_cast<float2*>(ws + plan.off_bh32) : nullptr,
       desc ? reinterpret_cast<BatchInst*>(ws + plan.off_desc) : nullptr, desc ? *desc : BatchInst());
   return cudaGetLastError();
 }

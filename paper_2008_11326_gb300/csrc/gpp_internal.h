@@ -28,7 +28,6 @@ struct FwdPlan {
   size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
   size_t off_bt32 = 0;    // FP32-bulk only: BandEntry32[B][W]
   size_t off_am32 = 0;    // FP32-bulk only: gathered weights c64[P][B]
-  size_t off_bh32 = 0;    // FP32-bulk only: float2[B], per band min(x rounded down), max(x rounded up)
   size_t gather_total = 0;
   size_t off_desc = 0;    // the instance descriptor (BatchInst)
   size_t off_counter = 0; // tile counter
@@ -79,7 +78,6 @@ struct BatchInst {
   const float2* am32 = nullptr;
   const BandEntry* bt = nullptr;
   const BandEntry32* bt32 = nullptr;
-  const float2* bh32 = nullptr;
   const int* colg = nullptr;
   const int* flags = nullptr;
   gpp_c128* ach = nullptr;

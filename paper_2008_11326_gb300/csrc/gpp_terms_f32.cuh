@@ -61,7 +61,7 @@ __device__ __forceinline__ float msel(unsigned m, float a, float b) {
 
 // Per-(igp, ig) constants of the FP32 path.
 struct PairF32 {
-  float wr, wi, wi2, mw2r, w2i, Iwr, Iwi;
+  float wr, wi, wi2, mw2r, w2i;
   float lo, hi;  // the warp's interval [min Re w - 1/2, max Re w + 1/2], widened by 2^-20
 };
 
@@ -80,15 +80,18 @@ struct F32Slots {
     return reinterpret_cast<const BandEntry**>(sp + 2 * 4 * W * blockDim.x + 4 * blockDim.x) +
            threadIdx.x;
   }
+  // I w of the thread's G-vector in FP32 (applied to the chunk sums only)
+  static __device__ __forceinline__ float2* iw(float* sp) {
+    return reinterpret_cast<float2*>(sp + 2 * 4 * W * blockDim.x + 6 * blockDim.x) + threadIdx.x;
+  }
 };
 
 // Bands [b0, b1) into the chunk sums c. OCC (whether these bands enter asxtemp) is a
 // template parameter: a runtime flag in this loop body costs instructions.
 template <int W, bool OCC>
-__device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float2* __restrict__ an_ptr,
+__device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* __restrict__ an_ptr,
                                           const float2* __restrict__ am_ptr,
-                                          const BandEntry32* __restrict__ bt32,
-                                          const float2* __restrict__ bh32, float* sp,
+                                          const BandEntry32* __restrict__ bt32, float* sp,
                                           const PairF32& q, float (&c)[4 * W]) {
   if (b0 >= b1) return;
   // the next band's aqsntemp and weight are loaded one band ahead (their global-memory
@@ -125,12 +128,14 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
         c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
       }
     };
-    const float2 h = __ldg(&bh32[b]);
-    if (h.x > q.hi || h.y < q.lo) {
+    // the band's frequency range (rounded outwards) rides in the first entry's a.w / b.w
+    const float4 e0a = __ldg(&e[0].a);
+    const float4 e0b = __ldg(&e[0].b);
+    if (e0a.w > q.hi || e0b.w < q.lo) {
       // every frequency of the band outside the warp's interval on the same side
 #pragma unroll
       for (int iw = 0; iw < W; ++iw) {
-        const float4 ea = __ldg(&e[iw].a);
+        const float4 ea = iw == 0 ? e0a : __ldg(&e[iw].a);
         const float Ar = ea.x - q.wr;
         const float A2 = fmaf(Ar, Ar, q.wi2);
         const float S2 = fmaf(ea.z, q.wr, A2);
@@ -141,8 +146,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
     }
 #pragma unroll
     for (int iw = 0; iw < W; ++iw) {
-      const float4 ea = __ldg(&e[iw].a);
-      const float4 eb = __ldg(&e[iw].b);
+      const float4 ea = iw == 0 ? e0a : __ldg(&e[iw].a);
+      const float4 eb = iw == 0 ? e0b : __ldg(&e[iw].b);
       const float x = ea.x, x2 = ea.y, x4 = ea.z;
       const float Ar = x - q.wr;
       const float A2 = fmaf(Ar, Ar, q.wi2);
@@ -185,7 +190,7 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
           // branch 2: K (-conj(S)/2) / |S|^2 = (Re K Yr - Im K Im w/2, Im K Yr + Re K Im w/2) b2
           const float wih = 0.5f * q.wi;
           const float coef = msel(m, r, b2);
-          const float Yr = msel(m, x2, ea.w) + msel(m, q.mw2r, -0.5f * q.wr);
+          const float Yr = msel(m, x2, -0.5f * x) + msel(m, q.mw2r, -0.5f * q.wr);
           const float ur = fmaf(msel(m, K2r, Kr), Yr, msel(m, P1r, -Ki * wih));
           const float ui = fmaf(msel(m, K2i, Ki), Yr, msel(m, P1i, Kr * wih));
           c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
@@ -198,9 +203,10 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int64_t G, const float
 
 // All bands of one (igp, ig) pair into the thread's compensated FP32 pairs hi + lo, which
 // live in shared memory (`sp`, layout [2][4W][blockDim.x] floats, then the threads' FP64
-// wtilde as double2[blockDim.x], then the FP64 band table pointer [blockDim.x]: touched once
-// per chunk, or only on the rare exact-decision path, they would otherwise hold registers
-// through the band loop, and the FP32 path is limited by occupancy). Bands are summed in
+// wtilde as double2[blockDim.x], the FP64 band table pointer [blockDim.x] and I w as
+// float2[blockDim.x]: touched once per chunk, or only on the rare exact-decision path, they
+// would otherwise hold registers through the band loop, and the FP32 path is limited by
+// occupancy). Bands are summed in
 // FP32 over chunks of kChunk bands and every chunk sum is added to the pair with Kahan's
 // compensation.
 template <int W>
@@ -208,7 +214,6 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
                                               const float2* __restrict__ an_ptr,
                                               const float2* __restrict__ am_ptr,
                                               const BandEntry32* __restrict__ bt32,
-                                              const float2* __restrict__ bh32,
                                               const BandEntry* __restrict__ bt64,
                                               double2 w64, double2 I64, bool live,
                                               float* sp) {
@@ -219,8 +224,7 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
   q.wi2 = q.wi * q.wi;
   q.mw2r = -fmaf(q.wr, q.wr, -q.wi2);   // -Re w^2
   q.w2i = 2.0f * q.wr * q.wi;           // Im w^2
-  q.Iwr = fmaf(Ir, q.wr, -Ii * q.wi);
-  q.Iwi = fmaf(Ir, q.wi, Ii * q.wr);
+  *F32Slots<W>::iw(sp) = make_float2(fmaf(Ir, q.wr, -Ii * q.wi), fmaf(Ir, q.wi, Ii * q.wr));
   *F32Slots<W>::w64(sp) = w64;
   *F32Slots<W>::bt64(sp) = bt64;
   {  // the warp's Re w interval (inert lanes, whose I is 0, left out)
@@ -245,14 +249,16 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
     const int bend = min(b0 + kChunk, B);
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
-    bands_f32<W, true>(b0, bocc, G, an_ptr, am_ptr, bt32, bh32, sp, q, c);
-    if (bocc < bend) bands_f32<W, false>(bocc, bend, G, an_ptr, am_ptr, bt32, bh32, sp, q, c);
+    bands_f32<W, true>(b0, bocc, static_cast<int>(G), an_ptr, am_ptr, bt32, sp, q, c);
+    if (bocc < bend)
+      bands_f32<W, false>(bocc, bend, static_cast<int>(G), an_ptr, am_ptr, bt32, sp, q, c);
     // the chunk sums times I w, merged into the pairs with Kahan's compensation (the pair
     // holds the running sum as hi + lo)
+    const float2 Iw = *F32Slots<W>::iw(sp);
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) {
       const float cr = c[k & ~1], ci = c[k | 1];
-      const float v = (k & 1) ? fmaf(q.Iwr, ci, q.Iwi * cr) : fmaf(q.Iwr, cr, -q.Iwi * ci);
+      const float v = (k & 1) ? fmaf(Iw.x, ci, Iw.y * cr) : fmaf(Iw.x, cr, -Iw.y * ci);
       float& hi = *F32Slots<W>::pair(sp, k);
       float& lo = *F32Slots<W>::pair(sp, 4 * W + k);
       const float y = v + lo;
