@@ -600,8 +600,8 @@ def run_pipe_rates():
     sink = torch.zeros(1, dtype=torch.float64, device=dev)
     out = {}
     for kind, iters in (("dfma", 256), ("dadd", 256), ("dmul", 256), ("drcp", 128),
-                        ("drcp_approx", 512), ("drcp_rn", 64), ("ffma", 8192),
-                        ("fsetp", 8192), ("isel", 8192)):
+                        ("drcp_approx", 512), ("drcp_rn", 64), ("f2f", 256), ("ffma", 8192),
+                        ("fsetp", 8192), ("isel", 8192), ("fsel", 8192)):
         blocks, threads = sms * 4, 256
         gpp.peak_launch(kind, max(iters // 8, 1), blocks, threads, sink)
         torch.cuda.synchronize(dev)
