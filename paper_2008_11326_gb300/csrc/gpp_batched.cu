@@ -22,6 +22,9 @@ namespace gpp {
 
 namespace {
 
+// Band count from which the FP32-bulk kernel sorts a tile's G-vectors by Re w.
+constexpr int kSortBands = 256;
+
 // Smallest power of two >= n (n >= 1).
 __host__ __device__ inline int pow2_ceil(int n) {
   int k = 1;
@@ -108,14 +111,16 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
     if (F32) {
 #pragma unroll
       for (int k = 0; k < 2 * 4 * W; ++k) s_pair[k * blockDim.x + threadIdx.x] = 0.0f;
-      // The tile's G-vectors in order of Re w, so that the 32 of a warp (consecutive in
-      // that order) span a narrow range of Re w and most frequencies fall outside it (the
-      // far-from-threshold path); inert positions sort last. The sum does not depend on
-      // which thread takes which G-vector.
+      // With at least kSortBands bands, the tile's G-vectors are taken in order of Re w, so
+      // that the 32 of a warp (consecutive in that order) span a narrow range of Re w and
+      // most frequencies fall outside it (the far-from-threshold path); inert positions
+      // sort last. With fewer bands the sort and the scattered loads it causes cost more
+      // than they save. The sum does not depend on which thread takes which G-vector.
+      const bool sort = B >= kSortBands;
       for (int q = threadIdx.x; q < sort_n; q += blockDim.x) {
         const int64_t ig = igt * tile_n + q;
         float key = __int_as_float(0x7f800000);
-        if (q < tile_n && ig < G && col_ok) {
+        if (sort && q < tile_n && ig < G && col_ok) {
           key = static_cast<float>(__ldg(&d.wt[p * G + ig].x));
           key = key == key ? key : 0.0f;  // a NaN must still sort among the live positions
         }
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
         s_pos[q] = q;
       }
       __syncthreads();
-      bitonic_sort(s_key, s_pos, sort_n);
+      if (sort) bitonic_sort(s_key, s_pos, sort_n);
     }
     for (int j = 0; j < igpt; ++j) {
       // F32: a padding position (>= tile_n, key +inf like an inert one) can sort into the
