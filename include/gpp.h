@@ -173,8 +173,8 @@ GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_
  * are copied into `workspace` (a device buffer of gpp_sigma_host_workspace_size() bytes),
  * the sum runs, the outputs are copied back, and the call returns after `stream` has
  * finished (it synchronises). The copies of aqsntemp, I_eps_array and wtilde_array go in
- * up to 8 chunks of G-vectors on a copy stream while the sum runs the chunks already
- * copied, alternating between `stream` and a second stream (the library creates both
+ * up to 8 chunks of G-vectors (of doubling size, so that the sum starts after a small
+ * first chunk) on a copy stream while the sum runs the chunks already copied, alternating between `stream` and a second stream (the library creates both
  * streams on a device's first call and keeps them); the result equals gpp_sigma's bit for
  * bit.
  */

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -776,8 +777,16 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   if (e == cudaSuccess) e = h2d(6, h.indinv, (G + 1) * 4);
   if (e == cudaSuccess) e = h2d(7, h.wx_array, B * W * 8);
   if (e == cudaSuccess) e = cudaEventRecord(ev.ev[1], hs.copy);
+  // Chunk sizes double (boundaries at nigt (2^k - 1) / (2^K - 1), each chunk at least one
+  // G-vector tile): the sum starts after a small first chunk has arrived, and every later
+  // chunk arrives while the ones before it are summed.
   std::vector<int64_t> igt0(K + 1);
-  for (int k = 0; k <= K; ++k) igt0[k] = nigt * k / K;
+  igt0[0] = 0;
+  for (int k = 1; k <= K; ++k) {
+    const int64_t geo = static_cast<int64_t>(
+        std::llround(static_cast<double>(nigt) * ((1ll << k) - 1) / ((1ll << K) - 1)));
+    igt0[k] = std::min<int64_t>(std::max<int64_t>(geo, igt0[k - 1] + 1), nigt - (K - k));
+  }
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     const int64_t c0 = igt0[k] * tile_ig, c1 = std::min<int64_t>(igt0[k + 1] * tile_ig, G);
     e = h2d_cols(1, h.aqsntemp, 16, B, c0, c1);

@@ -173,14 +173,17 @@ def test_host_entry_point_matches_device(gpp):
     assert np.array_equal(ach.numpy(), dev[0]) and np.array_equal(asx.numpy(), dev[1])
 
 
+@pytest.mark.parametrize("shape", [(60, 9001, 1100), (24, 32768, 1100)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
-def test_host_entry_point_pipelined_chunks(gpp, precision):
-    """An instance large enough for the host entry to overlap its copies with the sum in
-    several G-vector chunks on two streams: the result equals the device entry point's bit
-    for bit (every tile keeps its partial slot and one reduction sums them in order), also
-    with odd launch shapes and a ragged G."""
+def test_host_entry_point_pipelined_chunks(gpp, precision, shape):
+    """Instances large enough for the host entry to overlap its copies with the sum in
+    G-vector chunks of doubling size on two streams ((2P + B) G 16 B = 330 MB: 2 chunks;
+    1.2 GB: 8 chunks, the first of one G-vector tile): the result equals the device entry
+    point's bit for bit (every tile keeps its partial slot and one reduction sums them in
+    order), also with odd launch shapes and a ragged G."""
     import torch
-    prob = inputs.make_problem(60, 2, 9001, 1100, 3, seed=8)   # (2P + B) G 16 B = 330 MB
+    B, G, P = shape
+    prob = inputs.make_problem(B, 2, G, P, 3, seed=8)
     dev = gpp.DeviceProblem.from_host(prob, device="cuda", c64=precision == "fp32_bulk")
     hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True,
                                      c64=precision == "fp32_bulk")
