@@ -30,7 +30,8 @@ if ROOT not in sys.path:
 METRIC = "GPP FP64 TFLOP/s & %peak at 512x1638x32768x3; FP32-bulk speedup at <=1e-6 err"
 UNIT = "TFLOP/s"
 WORKLOAD = "gpp_benchmark_B512_P1638_G32768_nw3"
-ORACLE_SAMPLE_BANDS = 8
+ORACLE_SAMPLE_BANDS = 8          # bands per step of the reference arm (the oracle)
+CPU_BASELINE_SAMPLE_BANDS = 32   # bands of the cpu_baseline sample (~10 s on 16 cores)
 
 
 def parse():
@@ -46,11 +47,14 @@ def parse():
     ap.add_argument("--pipe-rates", action="store_true",
                     help="print the throughput of every instruction kind of the library's "
                          "throughput kernels (machine characterisation) and exit")
-    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32", "bwd", "batched"],
+    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32", "fwd_f32_sorted", "bwd",
+                                               "batched"],
                     default=None,
-                    help="run only a small case three times, for ncu captures: fwd_* and bwd "
-                         "use B=64, P=256, G=32768, nw=3 (0.3 GB of (igp, ig) arrays, more "
-                         "than L2); batched uses 8 instances with G in [2048, 32768] and B=32")
+                    help="run only a small case three times, for ncu captures: fwd_f64, "
+                         "fwd_f32 and bwd use B=64, P=256, G=32768, nw=3 (0.3 GB of (igp, ig) "
+                         "arrays, more than L2); fwd_f32_sorted B=256, P=128 (the FP32-bulk "
+                         "kernel sorts tiles from 256 bands); batched uses 8 instances with G "
+                         "in [2048, 32768] and B=32")
     return ap.parse_args()
 
 
@@ -525,7 +529,7 @@ def run_gpu(args):
     cpu = None
     if not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        v, dt, sub, ref = oracle_sample(prob, ORACLE_SAMPLE_BANDS, cores, want_result=True)
+        v, dt, sub, ref = oracle_sample(prob, CPU_BASELINE_SAMPLE_BANDS, cores, want_result=True)
         v1, dt1 = oracle_sample(prob, 1, 1)
         ref = np.concatenate(ref)
         parity = {}
@@ -536,11 +540,11 @@ def run_gpu(args):
             parity[prec] = float(np.max(np.abs(got - ref) / np.abs(ref)))
         del sdp
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {ORACLE_SAMPLE_BANDS} of 512 bands of the benchmark instance "
+               "sample": f"first {CPU_BASELINE_SAMPLE_BANDS} of 512 bands of the benchmark instance "
                          f"({dt:.1f} s, OpenMP over igp on all host cores)",
                "value_1_core": v1,
                "sample_1_core": f"first band of the benchmark instance ({dt1:.1f} s, one thread)",
-               "full_instance_s_extrapolated": dt * prob.number_bands / ORACLE_SAMPLE_BANDS,
+               "full_instance_s_extrapolated": dt * prob.number_bands / CPU_BASELINE_SAMPLE_BANDS,
                "gpu_max_rel_err_on_sample": parity}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -586,8 +590,11 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "batched", "achtemp0": str(outs[0][0][0].item())}))
         return 0
-    prob = inputs.make_problem(64, 2, 32768, 256, 3, seed=1)
-    precision = "fp32_bulk" if args.profile_case == "fwd_f32" else "fp64"
+    if args.profile_case == "fwd_f32_sorted":   # enough bands for the tile sort by Re w
+        prob = inputs.make_problem(256, 2, 32768, 128, 3, seed=1)
+    else:
+        prob = inputs.make_problem(64, 2, 32768, 256, 3, seed=1)
+    precision = "fp32_bulk" if args.profile_case.startswith("fwd_f32") else "fp64"
     dp = gpp.DeviceProblem.from_host(prob, device="cuda", c64=precision == "fp32_bulk")
     if args.profile_case == "bwd":
         ga, gs = inputs.cotangents(3, prob.nw)
