@@ -189,11 +189,15 @@ GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void
  * The scratch lives in a fixed array of GPP_NOALLOC_SCRATCH_BYTES inside the library,
  * which every GPU that loads the library holds until the process exits. The call allocates
  * nothing and frees nothing. Problems whose gpp_sigma_workspace_size() exceeds the array
- * are rejected with GPP_ERR_WORKSPACE (the benchmark shape B=512, P=1638, G=32768, nw=3
- * needs about 24 MB with the default tiles). The first call on a device looks up the array's device address with
+ * are rejected with GPP_ERR_WORKSPACE, unless `ig_per_thread` is 0 and deeper tiles (4,
+ * then 8 G-vectors per thread: fewer per-tile partials) fit, which the call then uses (the
+ * benchmark shape B=512, P=1638, G=32768, nw=3 needs about 24 MB in FP64 with the default
+ * tiles, 30 MB in FP32-bulk with 4 G-vectors per thread). The first call on a device looks
+ * up the array's device address with
  * that device current; make that first call before any stream capture. All calls share
  * the one array, so calls that overlap on the GPU (other streams, other threads) race:
- * serialise them. Results equal gpp_sigma's. Asynchronous on `stream`.
+ * serialise them. Results equal gpp_sigma's with the tile shape used. Asynchronous on
+ * `stream`.
  */
 #define GPP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 GPP_API int gpp_sigma_noalloc(const gpp_problem *prob, const gpp_options *opt, void *stream);

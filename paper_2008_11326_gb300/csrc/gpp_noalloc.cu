@@ -20,11 +20,30 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
+bool opt_default_depth(const gpp_options& o) { return o.ig_per_thread == 0; }
+
 }  // namespace
 
 extern "C" int gpp_sigma_noalloc(const gpp_problem* prob, const gpp_options* opt, void* stream) {
-  const size_t need = gpp_sigma_workspace_size(prob, opt);
+  gpp_options o;
+  if (opt) {
+    o = *opt;
+  } else {
+    gpp_options_default(&o);
+  }
+  size_t need = gpp_sigma_workspace_size(prob, &o);
   if (need == 0 && gpp_last_error()[0] != '\0') return GPP_ERR_BAD_SIZE;  // invalid arguments
+  // With the default tile depth, deeper tiles (fewer per-tile partial slots) may fit where
+  // the default does not; the result is the same sum up to the order of its partials.
+  for (int k = 4; need > GPP_NOALLOC_SCRATCH_BYTES && opt_default_depth(o) && k <= 8; k *= 2) {
+    gpp_options deeper = o;
+    deeper.ig_per_thread = k;
+    const size_t n = gpp_sigma_workspace_size(prob, &deeper);
+    if (n != 0 && n <= GPP_NOALLOC_SCRATCH_BYTES) {
+      o = deeper;
+      need = n;
+    }
+  }
   if (need > GPP_NOALLOC_SCRATCH_BYTES) {
     char msg[200];
     snprintf(msg, sizeof(msg),
@@ -48,5 +67,5 @@ extern "C" int gpp_sigma_noalloc(const gpp_problem* prob, const gpp_options* opt
     }
     ptr = g_scratch_ptr[dev];
   }
-  return gpp_sigma(prob, opt, ptr, GPP_NOALLOC_SCRATCH_BYTES, stream);
+  return gpp_sigma(prob, &o, ptr, GPP_NOALLOC_SCRATCH_BYTES, stream);
 }
