@@ -532,12 +532,17 @@ def run_gpu(args):
         v, dt, sub, ref = oracle_sample(prob, CPU_BASELINE_SAMPLE_BANDS, cores, want_result=True)
         v1, dt1 = oracle_sample(prob, 1, 1)
         ref = np.concatenate(ref)
-        parity = {}
+        parity, scaled, per_output = {}, {}, {}
         sdp = gpp.DeviceProblem.from_host(sub, device=device, c64=True)
         for prec in ("fp64", "fp32_bulk"):
             a, s = gpp.sigma(sdp, precision=prec)
             got = np.concatenate([a.cpu().numpy(), s.cpu().numpy()])
             parity[prec] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+            # the same errors against the sample's output scale (its largest |output|): an
+            # output much smaller than the others (cancellation over bands) has a relative
+            # error above the terms' rounding level
+            scaled[prec] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+            per_output[prec] = [float(e) for e in np.abs(got - ref) / np.abs(ref)]
         del sdp
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {CPU_BASELINE_SAMPLE_BANDS} of 512 bands of the benchmark instance "
@@ -545,7 +550,10 @@ def run_gpu(args):
                "value_1_core": v1,
                "sample_1_core": f"first band of the benchmark instance ({dt1:.1f} s, one thread)",
                "full_instance_s_extrapolated": dt * prob.number_bands / CPU_BASELINE_SAMPLE_BANDS,
-               "gpu_max_rel_err_on_sample": parity}
+               "gpu_max_rel_err_on_sample": parity,
+               "gpu_max_err_on_sample_vs_largest_output": scaled,
+               "gpu_rel_err_on_sample_per_output": per_output,
+               "sample_output_magnitudes": [float(a) for a in np.abs(ref)]}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
