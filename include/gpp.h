@@ -156,6 +156,8 @@ GPP_API size_t gpp_sigma_workspace_size(const gpp_problem *prob, const gpp_optio
  * gather, main sum over tiles taken from a counter by a persistent grid with one partial
  * per tile, fixed-order reduction of the partials) and returns without synchronising,
  * except with debug_checks = 1, where it synchronises `stream` to report bad indices.
+ * A problem with number_bands, ngpown or ncouls equal to 0 is an empty sum: the outputs
+ * are set to zero on `stream`, no input is read and the workspace may be NULL.
  * Errors: NULL_PTR, BAD_SIZE, BAD_OPTION, WORKSPACE, CUDA, BAD_INDEX (debug_checks only).
  */
 GPP_API int gpp_sigma(const gpp_problem *prob, const gpp_options *opt, void *workspace,
