@@ -359,6 +359,23 @@ def measure_large(torch, gpp, inputs, device):
     return out
 
 
+def max_over_ranks(value: float, pg=None, device="cpu") -> float:
+    """The largest of the ranks' values (each rank passes its own; all ranks get the
+    result). Without a process group, the value itself."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank: float, seconds_per_step: float, world: int) -> float:
+    """Every rank sums its own copy of the instance (replicas, weak scaling): the job does
+    world x the work in the slowest rank's time."""
+    return world * flops_per_rank / seconds_per_step / 1e12
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -415,12 +432,8 @@ def run_gpu(args):
     total_ms = t0.elapsed_time(t1)
     main_ms = [stage[k][1].elapsed_time(stage[k][2]) for k in range(K)]
     step_ms_each = [stage[k][0].elapsed_time(stage[k][3]) for k in range(K)]
-    step_ms = total_ms / K
-    if pg is not None:
-        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * flops / (step_ms * 1e-3) / 1e12
+    step_ms = max_over_ranks(total_ms / K, pg, device)
+    value = whole_job_tflops(flops, step_ms * 1e-3, world)
     deterministic = bool(np.array_equal(ach.cpu().numpy(), ref_a) and
                          np.array_equal(asx.cpu().numpy(), ref_s))
 
@@ -437,6 +450,7 @@ def run_gpu(args):
     for evs in e2e_stage:
         for e in evs:
             e.record()
+    barrier()
     torch.cuda.synchronize(device)
     with ClockSampler(local) as e2e_clk:
         s0 = time.perf_counter()
@@ -444,6 +458,8 @@ def run_gpu(args):
             e2e_start[k].record()
             gpp.sigma_host(hp, workspace=hws, out=hout, stage_events=e2e_stage[k])
         e2e_s = (time.perf_counter() - s0) / e2e_steps
+    barrier()
+    e2e_s = max_over_ranks(e2e_s, pg, device)
     e2e_ok = bool(np.array_equal(hout[0].numpy(), ref_a) and np.array_equal(hout[1].numpy(), ref_s))
     e2e_h2d_ms = statistics.mean(e2e_start[k].elapsed_time(e2e_stage[k][0]) for k in range(e2e_steps))
     e2e_main_ms = statistics.mean(e2e_stage[k][1].elapsed_time(e2e_stage[k][2])
@@ -566,7 +582,7 @@ def run_gpu(args):
             "peaks_measured": peaks,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * flops / e2e_s / 1e12, "unit": UNIT,
+            "e2e": {"value": whole_job_tflops(flops, e2e_s, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 2 * prob.nw * 16,
                     "steps": e2e_steps, "matches_device_result": e2e_ok,
                     "h2d_ms": e2e_h2d_ms, "main_kernel_ms": e2e_main_ms,
