@@ -53,7 +53,7 @@ def parse():
                     help="run only a small case three times, for ncu captures: fwd_f64, "
                          "fwd_f32 and bwd use B=64, P=256, G=32768, nw=3 (0.3 GB of (igp, ig) "
                          "arrays, more than L2); fwd_f32_sorted B=256, P=128 (the FP32-bulk "
-                         "kernel sorts tiles from 256 bands); batched uses 8 instances with G "
+                         "kernel sorts from 128 bands); batched uses 8 instances with G "
                          "in [2048, 32768] and B=32")
     return ap.parse_args()
 

@@ -123,7 +123,7 @@ typedef struct gpp_options {
     int32_t block_threads; /* threads per CTA of the main kernel: 0 = default (128), else a multiple of 32 in [64, 256] */
     int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = as many as fit */
     int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
-    int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4 FP64, 2 FP32-bulk), max 8; a tile is
+    int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4), max 8; a tile is
                               one igp column x block_threads * ig_per_thread G-vectors x all bands */
     int32_t physics;       /* bit set of gpp_physics: 0 = the paper's sum */
     int32_t reserved;      /* must be 0 */
@@ -191,12 +191,11 @@ GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void
  * The scratch lives in a fixed array of GPP_NOALLOC_SCRATCH_BYTES inside the library,
  * which every GPU that loads the library holds until the process exits. The call allocates
  * nothing and frees nothing. Problems whose gpp_sigma_workspace_size() exceeds the array
- * are rejected with GPP_ERR_WORKSPACE, unless `ig_per_thread` is 0 and deeper tiles (4,
- * then 8 G-vectors per thread: fewer per-tile partials) fit, which the call then uses (the
- * benchmark shape B=512, P=1638, G=32768, nw=3 needs about 24 MB in FP64 with the default
- * tiles, 30 MB in FP32-bulk with 4 G-vectors per thread). The first call on a device looks
- * up the array's device address with
- * that device current; make that first call before any stream capture. All calls share
+ * are rejected with GPP_ERR_WORKSPACE, unless `ig_per_thread` is 0 and tiles of 8
+ * G-vectors per thread (half the per-tile partials) fit, which the call then uses (the
+ * benchmark shape B=512, P=1638, G=32768, nw=3 needs about 24 MB in FP64 and 30 MB in
+ * FP32-bulk with the default tiles). The first call on a device looks up the array's
+ * device address with that device current; make that first call before any stream capture. All calls share
  * the one array, so calls that overlap on the GPU (other streams, other threads) race:
  * serialise them. Results equal gpp_sigma's with the tile shape used. Asynchronous on
  * `stream`.

@@ -110,10 +110,8 @@ int check_pointers(const gpp_problem& p, int precision, bool outputs = true) {
   return GPP_OK;
 }
 
-// Default G-vectors per thread of a tile: 4 for FP64; 2 for FP32-bulk, whose shorter
-// tiles balance better over 8 resident CTAs per SM (128x2 measured 1.2% faster than 128x4
-// on the 512-band benchmark instance, FP64 unchanged within noise).
-int default_igpt(bool f32) { return f32 ? 2 : 4; }
+// Default G-vectors per thread of a tile (both precisions).
+constexpr int kDefaultIgpt = 4;
 
 // Workspace layout of one instance. The gather segments come first; unless `gather_only`
 // (instances of a batched plan, the adjoint), the descriptor, tile counter and per-tile
@@ -124,7 +122,7 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
   pl.nw = static_cast<int>(p.nw);
   const bool f32 = o.precision == GPP_FP32_BULK;
   pl.threads = o.block_threads ? o.block_threads : 128;
-  pl.igpt = o.ig_per_thread ? o.ig_per_thread : default_igpt(f32);
+  pl.igpt = o.ig_per_thread ? o.ig_per_thread : kDefaultIgpt;
   if (degenerate(p)) {
     *plan = pl;
     return GPP_OK;
@@ -441,7 +439,7 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   bp->nw = static_cast<int>(probs[0].nw);
   bp->f32 = o.precision == GPP_FP32_BULK;
   bp->threads = o.block_threads ? o.block_threads : 128;
-  bp->igpt = o.ig_per_thread ? o.ig_per_thread : default_igpt(bp->f32);
+  bp->igpt = o.ig_per_thread ? o.ig_per_thread : kDefaultIgpt;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

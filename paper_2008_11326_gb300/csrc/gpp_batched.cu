@@ -23,7 +23,7 @@ namespace gpp {
 namespace {
 
 // Band count from which the FP32-bulk kernel sorts a tile's G-vectors by Re w.
-constexpr int kSortBands = 256;
+constexpr int kSortBands = 128;
 
 // Smallest power of two >= n (n >= 1).
 __host__ __device__ inline int pow2_ceil(int n) {
@@ -32,11 +32,13 @@ __host__ __device__ inline int pow2_ceil(int n) {
   return k;
 }
 
-// Sorts key[0, n) ascending and permutes idx with it (n a power of two; every thread of
-// the block takes part). A bitonic network: deterministic for fixed keys, and a
-// permutation of idx whatever the keys (NaN compares false and never swaps).
-__device__ inline void bitonic_sort(float* key, int* idx, int n) {
-  for (int k = 2; k <= n; k <<= 1) {
+// Sorts every aligned segment key[s seg, (s + 1) seg) of key[0, n) and permutes idx with
+// it (n and seg powers of two, seg <= n; every thread of the block takes part): even
+// segments ascending, odd ones descending (seg = n: all of it ascending). The first stages
+// of a bitonic network: deterministic for fixed keys, and a permutation of idx within each
+// segment whatever the keys (NaN compares false and never swaps).
+__device__ inline void bitonic_sort(float* key, int* idx, int n, int seg) {
+  for (int k = 2; k <= seg; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int l = i ^ j;
@@ -111,11 +113,14 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
     if (F32) {
 #pragma unroll
       for (int k = 0; k < 2 * 4 * W; ++k) s_pair[k * blockDim.x + threadIdx.x] = 0.0f;
-      // With at least kSortBands bands, the tile's G-vectors are taken in order of Re w, so
-      // that the 32 of a warp (consecutive in that order) span a narrow range of Re w and
-      // most frequencies fall outside it (the far-from-threshold path); inert positions
-      // sort last. With fewer bands the sort and the scattered loads it causes cost more
-      // than they save. The sum does not depend on which thread takes which G-vector.
+      // With at least kSortBands bands, the G-vectors of each pass over the tile (blockDim.x
+      // of them, when that is a power of two; else the whole tile) are taken in order of
+      // Re w, so that the 32 of a warp (consecutive in that order) span a narrow range of
+      // Re w and most frequencies fall outside it (the far-from-threshold path). Sorting
+      // within a pass keeps a warp's aqsntemp loads inside the pass's contiguous slice
+      // (blockDim.x x 8 bytes per band). With fewer bands the sort and the scattered loads
+      // cost more than they save. The sum does not depend on which thread takes which
+      // G-vector; inert positions (past G, dead column) carry +inf keys.
       const bool sort = B >= kSortBands;
       for (int q = threadIdx.x; q < sort_n; q += blockDim.x) {
         const int64_t ig = igt * tile_n + q;
@@ -128,11 +133,14 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
         s_pos[q] = q;
       }
       __syncthreads();
-      if (sort) bitonic_sort(s_key, s_pos, sort_n);
+      if (sort) {
+        const int nt = blockDim.x;
+        bitonic_sort(s_key, s_pos, sort_n, (nt & (nt - 1)) == 0 ? nt : sort_n);
+      }
     }
     for (int j = 0; j < igpt; ++j) {
       // F32: a padding position (>= tile_n, key +inf like an inert one) can sort into the
-      // first tile_n slots; it is inert
+      // first tile_n slots when the whole tile is sorted; it is inert
       const int q = F32 ? s_pos[j * blockDim.x + threadIdx.x] : 0;
       const int64_t ig = F32 ? igt * tile_n + q : (igt * igpt + j) * blockDim.x + threadIdx.x;
       const bool live = (!F32 || q < tile_n) && ig < G && col_ok;

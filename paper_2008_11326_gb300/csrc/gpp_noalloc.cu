@@ -33,11 +33,12 @@ extern "C" int gpp_sigma_noalloc(const gpp_problem* prob, const gpp_options* opt
   }
   size_t need = gpp_sigma_workspace_size(prob, &o);
   if (need == 0 && gpp_last_error()[0] != '\0') return GPP_ERR_BAD_SIZE;  // invalid arguments
-  // With the default tile depth, deeper tiles (fewer per-tile partial slots) may fit where
-  // the default does not; the result is the same sum up to the order of its partials.
-  for (int k = 4; need > GPP_NOALLOC_SCRATCH_BYTES && opt_default_depth(o) && k <= 8; k *= 2) {
+  // With the default tile depth, the deepest tiles (8 G-vectors per thread: half the
+  // per-tile partial slots) may fit where the default does not; the result is the same sum
+  // up to the order of its partials.
+  if (need > GPP_NOALLOC_SCRATCH_BYTES && opt_default_depth(o)) {
     gpp_options deeper = o;
-    deeper.ig_per_thread = k;
+    deeper.ig_per_thread = 8;
     const size_t n = gpp_sigma_workspace_size(prob, &deeper);
     if (n != 0 && n <= GPP_NOALLOC_SCRATCH_BYTES) {
       o = deeper;

@@ -63,16 +63,16 @@ def test_noalloc_matches_gpp_sigma_twice(gpp, name, shape):
 
 
 def test_noalloc_takes_deeper_tiles_when_the_default_does_not_fit(gpp):
-    """FP32-bulk at nw=8 with 1024 columns over 32768 G-vectors: the default tile (128 x 2
-    G-vectors) needs 32 MiB of partials alone, 4 G-vectors per thread half that. The call
-    then runs with 4 and equals gpp_sigma with that tile shape bit for bit."""
+    """FP32-bulk at nw=8 with 2560 columns over 32768 G-vectors: the default tile (128 x 4
+    G-vectors) needs 42 MB of partials, 8 G-vectors per thread half that. The call then
+    runs with 8 and equals gpp_sigma with that tile shape bit for bit."""
     import torch
-    dp = gpp.DeviceProblem(**inputs.make_device_arrays(8, 2, 32768, 1024, 8, seed=21,
+    dp = gpp.DeviceProblem(**inputs.make_device_arrays(8, 2, 32768, 2560, 8, seed=21,
                                                        device="cuda"))
     dp.make_c64()
     assert gpp.workspace_size(dp, precision="fp32_bulk") > 32 << 20
-    assert gpp.workspace_size(dp, precision="fp32_bulk", ig_per_thread=4) <= 32 << 20
-    a, s = gpp.sigma(dp, precision="fp32_bulk", ig_per_thread=4)
+    assert gpp.workspace_size(dp, precision="fp32_bulk", ig_per_thread=8) <= 32 << 20
+    a, s = gpp.sigma(dp, precision="fp32_bulk", ig_per_thread=8)
     torch.cuda.synchronize()
     got = _noalloc(gpp, dp, gpp.make_options(precision="fp32_bulk"))
     assert np.array_equal(got[0], a.cpu().numpy()) and np.array_equal(got[1], s.cpu().numpy())
