@@ -37,7 +37,7 @@ CPU_BASELINE_SAMPLE_BANDS = 32   # bands of the cpu_baseline sample (~10 s on 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpp", "reference"], default="gpp")
     ap.add_argument("--e2e-steps", type=int, default=2)
