@@ -73,13 +73,35 @@ class DeviceProblem:
     def device(self):
         return self.aqsmtemp.device
 
+    def check(self, ach: torch.Tensor | None = None, asx: torch.Tensor | None = None):
+        """Raise ValueError unless every array has the dtype, shape, device and layout that
+        include/gpp.h requires for these sizes (the library reads exactly those extents, so
+        a mismatch would read outside the tensors)."""
+        B, G, P, W = self.number_bands, self.ncouls, self.ngpown, self.nw
+        spec = [("aqsmtemp", torch.complex128, (B, G)), ("aqsntemp", torch.complex128, (B, G)),
+                ("I_eps_array", torch.complex128, (P, G)),
+                ("wtilde_array", torch.complex128, (P, G)), ("vcoul", torch.float64, (G,)),
+                ("inv_igp_index", torch.int32, (P,)), ("indinv", torch.int32, (G + 1,)),
+                ("wx_array", torch.float64, (B, W))]
+        if self.aqsntemp_c64 is not None:
+            spec.append(("aqsntemp_c64", torch.complex64, (B, G)))
+        dev = self.aqsmtemp.device
+        for name, dt, shape in spec:
+            x = getattr(self, name)
+            if (x.dtype != dt or tuple(x.shape) != shape or x.device != dev
+                    or not x.is_contiguous()):
+                raise ValueError(f"{name}: want a contiguous {dt} tensor of shape {shape} on "
+                                 f"{dev}, got {x.dtype} {tuple(x.shape)} on {x.device}")
+        for name, x in (("achtemp", ach), ("asxtemp", asx)):
+            if x is not None and (x.dtype != torch.complex128 or x.numel() < W
+                                  or x.device != dev or not x.is_contiguous()):
+                raise ValueError(f"{name}: want a contiguous complex128 tensor of at least "
+                                 f"{W} values on {dev}")
+
     def struct(self, ach: torch.Tensor, asx: torch.Tensor) -> N.GppProblem:
         def ptr(x):
             return None if x is None else x.data_ptr()
-        for f in _C128 + ("vcoul", "inv_igp_index", "indinv", "wx_array"):
-            x = getattr(self, f)
-            if not x.is_contiguous():
-                raise ValueError(f"{f} must be contiguous")
+        self.check(ach, asx)
         return N.GppProblem(
             self.number_bands, self.nvband, self.ncouls, self.ngpown, self.nw,
             ptr(self.aqsmtemp), ptr(self.aqsntemp), ptr(self.I_eps_array),
