@@ -16,7 +16,8 @@ measured memory bandwidth).
 
 It is a measurement tool beside the library: ``ncu_command`` builds the capture command,
 ``load_raw_csv`` reads ``ncu -i REPORT --page raw --csv``, ``summarize`` computes the
-roofline and ``to_markdown`` renders it. ``python -m paper_2008_11326_gb300.roofline REPORT
+roofline and ``to_markdown`` renders it; ``collect`` runs the capture and the first three
+steps in one call. ``python -m paper_2008_11326_gb300.roofline REPORT
 --fp64-peak-tflops X --hbm-gbs Y`` does all three on an existing report.
 """
 
@@ -78,10 +79,21 @@ def load_raw_csv(text: str, launch: int = 0) -> dict:
     return out
 
 
-def report_metrics(report: str, launch: int = 0) -> dict:
-    text = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], check=True,
-                          capture_output=True, text=True).stdout
+def report_metrics(report: str, launch: int = 0, run=subprocess.run) -> dict:
+    text = run(["ncu", "-i", report, "--page", "raw", "--csv"], check=True,
+               capture_output=True, text=True).stdout
     return load_raw_csv(text, launch)
+
+
+def collect(cmd, kernel_regex: str, report: str, peaks: dict, units: float | None = None,
+            skip: int = 0, count: int = 1, launch: int = 0, run=subprocess.run) -> dict:
+    """Capture, read back and summarise in one call: runs ``ncu_command`` on ``cmd`` (which
+    must already have exited 0 on the same GPU without ncu), then ``summarize`` on launch
+    ``launch`` of the report. Capture a small case of the kernel: the metric set takes
+    several replay passes per launch."""
+    run(ncu_command(cmd, kernel_regex, report, skip, count), check=True)
+    path = report if report.endswith(".ncu-rep") else report + ".ncu-rep"
+    return summarize(report_metrics(path, launch, run), peaks, units)
 
 
 def _count(m, op):

@@ -51,3 +51,22 @@ def test_cli_reads_csv_on_stdin(monkeypatch, capsys):
     assert roofline.main(["-", "--fp64-peak-tflops", "1.2", "--json"]) == 0
     s = json.loads(capsys.readouterr().out)
     assert s["fp64"]["frac_of_peak"] == pytest.approx(17e6 / 2.5e-3 / 1e12 / 1.2)
+
+
+def test_collect_runs_the_capture_then_reads_the_report():
+    calls = []
+
+    class Done:
+        stdout = CSV
+
+    def fake_run(args, **kw):
+        calls.append(list(args))
+        return Done()
+
+    s = roofline.collect(["python", "bench.py", "--profile-case", "fwd_f64"], "gpp_batched",
+                         "prof", {"fp64_tflops": 1.2}, units=1e6, run=fake_run)
+    assert calls[0][0] == "ncu" and calls[0][-4:] == ["python", "bench.py", "--profile-case",
+                                                      "fwd_f64"]
+    assert calls[0][calls[0].index("--clock-control") + 1] == "none"
+    assert calls[1] == ["ncu", "-i", "prof.ncu-rep", "--page", "raw", "--csv"]
+    assert s["fp64"]["flops_per_unit"] == pytest.approx(17.0)
