@@ -2,7 +2,7 @@
  * libgpp machine characterisation and numerics diagnostics.
  *
  * The paper reports its kernel against measured machine peaks (§I, the Empirical Roofline
- * Toolkit; §III v8, the FMA-ratio-adjusted FP64 peak). MEASURED copy bandwidth and bf16
+ * Toolkit; §III v8, the FMA-ratio-adjusted FP64 peak). Copy-bandwidth and bf16
  * GEMM rates do not cover the FP64 and FP32 pipes that bound the GPP sum, so the library
  * carries its own throughput kernels. Conventions as in gpp.h (device pointers, async on
  * `stream`, negative gpp_status on error, gpp_last_error()).
