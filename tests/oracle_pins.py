@@ -6,7 +6,8 @@ committed oracle; ``test_oracle_mutants.py`` runs them against copies of the ora
 planted mistake and checks that some pin fails for every mistake.
 
 Sources of truth:
-* hand-derived closed forms at size 1 and one hand-derived multi-index case
+* hand-derived closed forms at size 1, one hand-derived multi-index case and two exact
+  cancellation cases for the compensated summation
   (``tests/golden/closed_forms.json``, derivations inside);
 * an independent pure-Python brute force on tiny inputs;
 * invariants that follow from the structure of the sum (linearity, conjugation symmetry,
@@ -134,6 +135,46 @@ def pin_adjoint_physics(orc):
         for name, want in g[key].items():
             if not _close(out[name][0, 0], cfrac(want)):
                 fails.append(f"adjoint_physics {key} d/d{name}: got {out[name][0, 0]}")
+    return fails
+
+
+def summation_problems():
+    """The two cancellation cases of the golden file: bands summed within one column, and
+    column partials combined across columns."""
+    g = golden()["summation"]
+    one = np.ones((1, 1), np.complex128)
+    bands = g["bands"]
+    aqsn = np.array([[complex(float(Fraction(r)), float(Fraction(i)))]
+                     for r, i in zip(bands["aqsn_re"], bands["aqsn_im"])], np.complex128)
+    B = aqsn.shape[0]
+    pb = inputs.GppProblem(
+        number_bands=B, nvband=B, ncouls=1, ngpown=1, nw=1,
+        aqsmtemp=np.ones((B, 1), np.complex128), aqsntemp=aqsn, I_eps_array=one.copy(),
+        wtilde_array=one.copy(), vcoul=np.ones(1), inv_igp_index=np.zeros(1, np.int32),
+        indinv=np.array([0, 1], np.int32), wx_array=np.full((B, 1), 3.0))
+    cols = g["columns"]
+    eps = np.array([[float(Fraction(v))] for v in cols["I_eps"]], np.complex128)
+    P = eps.shape[0]
+    pc = inputs.GppProblem(
+        number_bands=1, nvband=1, ncouls=1, ngpown=P, nw=1, aqsmtemp=one.copy(),
+        aqsntemp=np.array([[cfrac(cols["aqsn"])]], np.complex128), I_eps_array=eps,
+        wtilde_array=np.ones((P, 1), np.complex128), vcoul=np.ones(1),
+        inv_igp_index=np.zeros(P, np.int32), indinv=np.array([0, 1], np.int32),
+        wx_array=np.full((1, 1), 3.0))
+    return (("bands", pb), ("columns", pc))
+
+
+def pin_compensated_summation(orc):
+    """Exact sums that a plain FP64 running sum gets wrong (every term exact, see the golden
+    file): the oracle's compensated summation within a column and across columns."""
+    fails = []
+    g = golden()["summation"]
+    for name, prob in summation_problems():
+        ach, asx = orc.sigma(prob)
+        want_a, want_s = cfrac(g[name]["ach"]), cfrac(g[name]["asx"])
+        if not (ach[0] == want_a and asx[0] == want_s):
+            fails.append(f"compensated summation over {name}: got {ach[0]}, {asx[0]}, "
+                         f"want {want_a}, {want_s}")
     return fails
 
 
@@ -360,5 +401,6 @@ def pin_adjoint_fd(orc, n_per_kind=4):
 
 
 ALL_PINS = (pin_closed_forms, pin_physics_closed_forms, pin_index_case,
+            pin_compensated_summation,
             pin_adjoint_closed_forms, pin_adjoint_physics, pin_brute_force, pin_invariants,
             pin_adjoint_fd)

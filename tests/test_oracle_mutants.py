@@ -50,6 +50,15 @@ MUTANTS = {
     "half factor on asx too": ("cplx s = occ * (M * ssx);", "cplx s = (ch_half ? 0.5 : 1.0) * occ * (M * ssx);"),
     "adjoint half factor dropped": ("cplx ca = (ch_half ? 0.5 : 1.0) * conj(ga[iw])", "cplx ca = conj(ga[iw])"),
     "adjoint cut derivative kept": ("    if (cut) { /* ssx", "    if (0) { /* ssx"),
+    "compensation dropped": ("{ return a->s + a->c; }", "{ return a->s; }"),
+    "compensation not accumulated": ("        a->c += (a->s - s) + t;\n    else\n        a->c += (t - s) + a->s;",
+                                     "        (void)0;\n    else\n        (void)0;"),
+    "compensation branches swapped": ("        a->c += (a->s - s) + t;\n    else\n        a->c += (t - s) + a->s;",
+                                      "        a->c += (t - s) + a->s;\n    else\n        a->c += (a->s - s) + t;"),
+    "compensation test on signed values": ("if (fabs(a->s) >= fabs(t))", "if (a->s >= t)"),
+    "column combine drops the compensation": ("            nsum_add(&tot, part[p * nacc + k].c);\n", ""),
+    "column combine uncompensated": ("            nsum_add(&tot, part[p * nacc + k].s);\n            nsum_add(&tot, part[p * nacc + k].c);",
+                                     "            tot.s += part[p * nacc + k].s + part[p * nacc + k].c;"),
 }
 
 
