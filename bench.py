@@ -47,12 +47,14 @@ def parse():
     ap.add_argument("--pipe-rates", action="store_true",
                     help="print the throughput of every instruction kind of the library's "
                          "throughput kernels (machine characterisation) and exit")
-    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f32", "fwd_f32_sorted", "bwd",
-                                               "batched"],
+    ap.add_argument("--profile-case", choices=["fwd_f64", "fwd_f64_b512", "fwd_f32",
+                                               "fwd_f32_sorted", "bwd", "batched"],
                     default=None,
                     help="run only a small case three times, for ncu captures: fwd_f64, "
                          "fwd_f32 and bwd use B=64, P=256, G=32768, nw=3 (0.3 GB of (igp, ig) "
-                         "arrays, more than L2); fwd_f32_sorted B=256, P=128 (the FP32-bulk "
+                         "arrays, more than L2); fwd_f64_b512 B=512, P=64, G=32768 (the "
+                         "benchmark's band count and G on 64 columns, 0.3 GB); "
+                         "fwd_f32_sorted B=256, P=128 (the FP32-bulk "
                          "kernel sorts from 128 bands); batched uses 8 instances with G "
                          "in [2048, 32768] and B=32")
     return ap.parse_args()
@@ -264,65 +266,88 @@ def measure_adjoint(torch, gpp, inputs, device, reps=3):
             "backward_over_forward": b / f, "target_max_ratio": 3.0}
 
 
-def measure_batched(torch, gpp, inputs, device):
+BATCH_REPS = 5             # timed repetitions of every arm of the batched comparison
+BATCH_FP64_BANDS = 64      # bands per instance in the FP64 batched comparison
+
+
+def _spread(ms):
+    return {"median_ms": statistics.median(ms), "min_ms": min(ms), "max_ms": max(ms),
+            "reps": len(ms)}
+
+
+def measure_batched(torch, gpp, inputs, device, reps=BATCH_REPS):
     """64 uneven instances: one graph-replayed persistent launch (autotuned tile shape)
-    against a loop of per-instance gpp_sigma calls, FP64 and FP32-bulk."""
+    against loops of per-instance gpp_sigma calls, both at the default tile and at the tuned
+    one, each arm timed ``reps`` times (median and spread). FP32-bulk on the full instances;
+    FP64 on the first BATCH_FP64_BANDS bands of every instance (the full FP64 batch takes
+    ~24 s per run)."""
     from paper_2008_11326_gb300 import autotune
     shapes = inputs.batched_shapes()
-    dps = [gpp.DeviceProblem(**inputs.make_device_arrays(**s, device=device)) for s in shapes]
-    units = sum(d.number_bands * d.ngpown * d.ncouls for d in dps)
-    flops = sum(inputs.model_flops(d.number_bands, d.ngpown, d.ncouls, d.nw) for d in dps)
+    full = [gpp.DeviceProblem(**inputs.make_device_arrays(**s, device=device)) for s in shapes]
+
+    def first_bands(d, nb):
+        nb = min(nb, d.number_bands)
+        return gpp.DeviceProblem(nb, d.nvband, d.ncouls, d.ngpown, d.nw, d.aqsmtemp[:nb],
+                                 d.aqsntemp[:nb], d.I_eps_array, d.wtilde_array, d.vcoul,
+                                 d.inv_igp_index, d.indinv, d.wx_array[:nb])
+
     out = {"workload": "64 instances, G log-uniform in [2048, 32768], P = G/20, B ~ U{64..512}, "
-                       "nw=3 (inputs drawn on the device)",
-           "units": units, "model_flop": flops}
-    for precision, reps in (("fp64", 1), ("fp32_bulk", 3)):
+                       "nw=3 (inputs drawn on the device)"}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(device)
+        ms = []
+        for _ in range(reps):
+            e = _events(torch, 2)
+            e[0].record()
+            fn()
+            e[1].record()
+            e[1].synchronize()
+            ms.append(e[0].elapsed_time(e[1]))
+        return ms
+
+    for precision in ("fp64", "fp32_bulk"):
+        dps = [first_bands(d, BATCH_FP64_BANDS) for d in full] if precision == "fp64" else full
         if precision == "fp32_bulk":
             for d in dps:
                 d.make_c64()
+        units = sum(d.number_bands * d.ngpown * d.ncouls for d in dps)
+        flops = sum(inputs.model_flops(d.number_bands, d.ngpown, d.ncouls, d.nw) for d in dps)
         tuned = autotune.tune_batched(dps, precision=precision, reps=1,
-                                      proxy_fraction=1 / 64 if precision == "fp64" else 1 / 32)
-        plan = gpp.BatchedPlan(dps, use_graph=True, precision=precision,
-                               block_threads=tuned["block_threads"],
-                               ig_per_thread=tuned["ig_per_thread"])
-        if reps > 1:
-            plan.run()
-        torch.cuda.synchronize(device)
-        g_ms = []
-        for _ in range(reps):
-            e = _events(torch, 2)
-            e[0].record()
-            plan.run()
-            e[1].record()
-            e[1].synchronize()
-            g_ms.append(e[0].elapsed_time(e[1]))
+                                      proxy_fraction=1 / 16 if precision == "fp64" else 1 / 32)
+        tile = dict(block_threads=tuned["block_threads"], ig_per_thread=tuned["ig_per_thread"])
+        plan = gpp.BatchedPlan(dps, use_graph=True, precision=precision, **tile)
+        g_ms = timed(plan.run)
         batched_res = [torch.cat(o).cpu() for o in plan.outputs]
         plan.close()
-        wss = [torch.empty(gpp.workspace_size(d, precision=precision), dtype=torch.uint8,
-                           device=device) for d in dps]
-        if reps > 1:
-            for d, w in zip(dps, wss):
-                gpp.sigma(d, workspace=w, precision=precision)
-        torch.cuda.synchronize(device)
-        l_ms = []
+        arms = {}
         loop_res = None
-        for _ in range(reps):
-            e = _events(torch, 2)
-            e[0].record()
-            res = [gpp.sigma(d, workspace=w, precision=precision) for d, w in zip(dps, wss)]
-            e[1].record()
-            e[1].synchronize()
-            l_ms.append(e[0].elapsed_time(e[1]))
-            loop_res = [torch.cat(r).cpu() for r in res]
-        del wss
+        for name, opts in (("loop_default_tile", {}), ("loop_tuned_tile", tile)):
+            wss = [torch.empty(gpp.workspace_size(d, precision=precision, **opts),
+                               dtype=torch.uint8, device=device) for d in dps]
+            res = []
+
+            def loop():
+                res[:] = [gpp.sigma(d, workspace=w, precision=precision, **opts)
+                          for d, w in zip(dps, wss)]
+            arms[name] = timed(loop)
+            if name == "loop_default_tile":
+                loop_res = [torch.cat(r).cpu() for r in res]
+            del wss
         diff = max(float(((a - b).abs() / b.abs()).max()) for a, b in zip(batched_res, loop_res))
-        out[precision] = {"graph_ms": min(g_ms), "loop_ms": min(l_ms),
-                          "speedup_vs_loop": min(l_ms) / min(g_ms),
-                          "tflops_model_graph": flops / (min(g_ms) * 1e-3) / 1e12,
-                          "tile": {"block_threads": tuned["block_threads"],
-                                   "ig_per_thread": tuned["ig_per_thread"],
-                                   "from_cache": tuned["cached"]},
-                          "max_rel_diff_vs_loop": diff}
-    del dps
+        g_med = statistics.median(g_ms)
+        out[precision] = {
+            "bands": f"first {BATCH_FP64_BANDS} of each instance" if precision == "fp64" else "all",
+            "units": units, "model_flop": flops,
+            "graph": _spread(g_ms),
+            **{k: _spread(v) for k, v in arms.items()},
+            "speedup_vs_loop_default_tile": statistics.median(arms["loop_default_tile"]) / g_med,
+            "speedup_vs_loop_tuned_tile": statistics.median(arms["loop_tuned_tile"]) / g_med,
+            "tflops_model_graph": flops / (g_med * 1e-3) / 1e12,
+            "tile": {**tile, "from_cache": tuned["cached"]},
+            "max_rel_diff_vs_loop": diff}
+    del full
     torch.cuda.empty_cache()
     return out
 
@@ -467,7 +492,35 @@ def run_gpu(args):
     del hws, hp
     torch.cuda.empty_cache()
 
-    # FP32-bulk forward on the same instance: speedup over FP64 and error against it
+    # FP32-bulk forward on the same instance: speedup over FP64 and error against it.
+    # (a) each call converts aqsntemp to complex64 in its own workspace (no copy kept by the
+    # caller); (b) the caller keeps the copy, made once by the library's conversion kernel.
+    def time_f32(dpx, ws_x):
+        for _ in range(W):
+            gpp.sigma(dpx, out=(ach, asx), workspace=ws_x, precision="fp32_bulk")
+        st = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+        for evs in st:
+            for e in evs:
+                e.record()
+        torch.cuda.synchronize(device)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for k in range(K):
+            gpp.sigma(dpx, out=(ach, asx), workspace=ws_x, precision="fp32_bulk",
+                      stage_events=st[k])
+        f1.record()
+        torch.cuda.synchronize(device)
+        return (f0.elapsed_time(f1) / K,
+                statistics.mean(st[k][0].elapsed_time(st[k][1]) for k in range(K)),
+                statistics.mean(st[k][1].elapsed_time(st[k][2]) for k in range(K)))
+
+    import dataclasses
+    dp_nc = dataclasses.replace(dp, aqsntemp_c64=None)
+    ws32 = torch.empty(gpp.workspace_size(dp_nc, precision="fp32_bulk"), dtype=torch.uint8,
+                       device=device)
+    f32c_step_ms, f32c_prep_ms, _ = time_f32(dp_nc, ws32)
+    got_c = np.concatenate([ach.cpu().numpy(), asx.cpu().numpy()])
+    del ws32, dp_nc
     c0 = torch.cuda.Event(enable_timing=True)
     c1 = torch.cuda.Event(enable_timing=True)
     c0.record()
@@ -477,31 +530,21 @@ def run_gpu(args):
     conv_ms = c0.elapsed_time(c1)
     ws32 = torch.empty(gpp.workspace_size(dp, precision="fp32_bulk"), dtype=torch.uint8,
                        device=device)
-    for _ in range(W):
-        gpp.sigma(dp, out=(ach, asx), workspace=ws32, precision="fp32_bulk")
-    stage32 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    for evs in stage32:
-        for e in evs:
-            e.record()
-    torch.cuda.synchronize(device)
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    f0.record()
-    for k in range(K):
-        gpp.sigma(dp, out=(ach, asx), workspace=ws32, precision="fp32_bulk",
-                  stage_events=stage32[k])
-    f1.record()
-    torch.cuda.synchronize(device)
-    f32_step_ms = f0.elapsed_time(f1) / K
-    f32_main_ms = statistics.mean(stage32[k][1].elapsed_time(stage32[k][2]) for k in range(K))
+    f32_step_ms, f32_prep_ms, f32_main_ms = time_f32(dp, ws32)
     got = np.concatenate([ach.cpu().numpy(), asx.cpu().numpy()])
     ref = np.concatenate([ref_a, ref_s])
     f32_err = float(np.max(np.abs(got - ref) / np.abs(ref)))
+    conv_bytes = prob.number_bands * prob.ncouls * (16 + 8)
     fp32_bulk = {"ms_per_step": f32_step_ms, "main_kernel_ms": f32_main_ms,
                  "tflops_model": flops / (f32_step_ms * 1e-3) / 1e12,
                  "speedup_vs_fp64": step_ms / f32_step_ms,
-                 "speedup_incl_c64_copy": step_ms / (f32_step_ms + conv_ms),
-                 "c64_copy_ms": conv_ms,
+                 "ms_per_step_converting_in_call": f32c_step_ms,
+                 "speedup_incl_c64_conversion": step_ms / f32c_step_ms,
+                 "gather_ms": f32_prep_ms,
+                 "gather_plus_conversion_ms": f32c_prep_ms,
+                 "c64_conversion_ms": conv_ms,
+                 "c64_conversion_gbs": conv_bytes / (conv_ms * 1e-3) / 1e9,
+                 "conversion_in_call_bit_equal": bool(np.array_equal(got_c, got)),
                  "max_rel_err_vs_fp64_gpu": f32_err,
                  "per_output_rel_err": [float(v) for v in np.abs(got - ref) / np.abs(ref)],
                  "fp32_peak_frac_model": flops / (f32_main_ms * 1e-3) / 1e12 / peaks["fp32_tflops"]}
@@ -541,6 +584,10 @@ def run_gpu(args):
                                 "fma_ratio": ex["fma_ratio"], "fma_adjusted_peak": adj,
                                 "frac_of_fma_adjusted_peak": exe / adj,
                                 "source": "ncu SASS counters of the same kernel, " + ex["workload"]}
+        # the same two fractions at the top of the roofline object: executed FP64 FLOP/s
+        # against the DFMA-chain peak, and against the FMA-adjusted peak (paper §III v8)
+        roofline["frac_executed"] = exe / peaks["fp64_tflops"]
+        roofline["frac_fma_adjusted"] = exe / adj
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -616,6 +663,8 @@ def run_profile_case(args):
         return 0
     if args.profile_case == "fwd_f32_sorted":   # enough bands for the tile sort by Re w
         prob = inputs.make_problem(256, 2, 32768, 128, 3, seed=1)
+    elif args.profile_case == "fwd_f64_b512":   # the benchmark's B and G, 64 columns
+        prob = inputs.make_problem(512, 2, 32768, 64, 3, seed=1)
     else:
         prob = inputs.make_problem(64, 2, 32768, 256, 3, seed=1)
     precision = "fp32_bulk" if args.profile_case.startswith("fwd_f32") else "fp64"

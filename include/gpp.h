@@ -108,8 +108,10 @@ typedef struct gpp_problem {
     const int32_t *inv_igp_index; /* [P] */
     const int32_t *indinv;        /* [G + 1] */
     const double *wx_array;       /* [B][W] */
-    /* complex64 copy of aqsntemp, read by GPP_FP32_BULK for its per-band loads (NULL
-     * otherwise). The (igp, ig) arrays are read once per pair in FP64 and rounded in
+    /* complex64 copy of aqsntemp, read by GPP_FP32_BULK for its per-band loads (ignored
+     * otherwise). NULL lets the library make it: the call then converts aqsntemp into its
+     * workspace first (an HBM-bound copy, counted in gpp_sigma_workspace_size: B * G * 8
+     * bytes more). The (igp, ig) arrays are read once per pair in FP64 and rounded in
      * registers, and the gathered weights are rounded by the gather kernel, so no other
      * copies are needed. */
     const gpp_c64 *aqsntemp_c64; /* [B][G] */
@@ -194,11 +196,15 @@ GPP_API int gpp_sigma_host(const gpp_problem *prob, const gpp_options *opt, void
  * are rejected with GPP_ERR_WORKSPACE, unless `ig_per_thread` is 0 and tiles of 8
  * G-vectors per thread (half the per-tile partials) fit, which the call then uses (the
  * benchmark shape B=512, P=1638, G=32768, nw=3 needs about 24 MB in FP64 and 30 MB in
- * FP32-bulk with the default tiles). The first call on a device looks up the array's
- * device address with that device current; make that first call before any stream capture. All calls share
- * the one array, so calls that overlap on the GPU (other streams, other threads) race:
- * serialise them. Results equal gpp_sigma's with the tile shape used. Asynchronous on
- * `stream`.
+ * FP32-bulk with the default tiles). Every call looks up the array's device address in
+ * the current device's context (cudaGetSymbolAddress), so a call on another device, in
+ * another context or after a device reset uses that context's copy; the first call on a
+ * device can load the library's device code, so make it before any stream capture. All
+ * calls share the one array, so calls that overlap on the GPU (other streams, other
+ * threads) race: serialise them. Everything that must start at zero is cleared by every
+ * call. Results equal gpp_sigma's with the tile shape used, bit for bit. Asynchronous on
+ * `stream`. Errors as gpp_sigma (NULL_PTR, BAD_SIZE, BAD_OPTION, ... with the same codes),
+ * plus WORKSPACE for a problem beyond the array and CUDA if the lookup fails.
  */
 #define GPP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 GPP_API int gpp_sigma_noalloc(const gpp_problem *prob, const gpp_options *opt, void *stream);
@@ -261,6 +267,13 @@ GPP_API int gpp_batched_plan_destroy(gpp_batched_plan *plan);
 /* One-shot: create (no graph), run, destroy. */
 GPP_API int gpp_sigma_batched(const gpp_problem *probs, int n, const gpp_options *opt,
                               void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * dst[i] = src[i] rounded to complex64 (round to nearest, both parts), i < n: the complex64
+ * copy of aqsntemp that GPP_FP32_BULK reads, made once by a caller that keeps it across
+ * calls. Device arrays; asynchronous on `stream`. Errors: NULL_PTR, BAD_SIZE (n < 0), CUDA.
+ */
+GPP_API int gpp_convert_c64(const gpp_c128 *src, gpp_c64 *dst, int64_t n, void *stream);
 
 /* Thread-local description of the last error on this host thread ("" if none). */
 GPP_API const char *gpp_last_error(void);

@@ -52,6 +52,16 @@ GPP_API int gpp_peak_launch(int kind, int64_t iters, int blocks, int threads, do
  */
 GPP_API int gpp_diag_rcp(const double *in, double *out, int64_t n, void *stream);
 
+/*
+ * Host-side fault injection for tests of the error paths. After this call, the n-th CUDA
+ * runtime call whose status a libgpp entry point checks on this host thread (1 = the next
+ * one) reports failure as if it had failed: the call itself has been made, and the entry
+ * point takes its error path (GPP_ERR_CUDA, with "[injected by
+ * gpp_diag_inject_cuda_failure]" in gpp_last_error()). Nothing fails on the device. n <= 0
+ * disarms; a countdown not reached stays armed.
+ */
+GPP_API void gpp_diag_inject_cuda_failure(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,10 +79,12 @@ SIGNATURES = [
     ("gpp_sigma_batched", ctypes.c_int,
      [ctypes.POINTER(GppProblem), ctypes.c_int, ctypes.POINTER(GppOptions), _vp,
       ctypes.c_size_t, _vp]),
+    ("gpp_convert_c64", ctypes.c_int, [_vp, _vp, _i64, _vp]),
     ("gpp_last_error", ctypes.c_char_p, []),
     ("gpp_version", ctypes.c_char_p, []),
     ("gpp_peak_launch", ctypes.c_int, [ctypes.c_int, _i64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     ("gpp_diag_rcp", ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    ("gpp_diag_inject_cuda_failure", None, [ctypes.c_int]),
 ]
 
 _lock = threading.Lock()

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gpp.h"
+#include "gpp_diag.h"
 #include "gpp_internal.h"
 
 namespace {
@@ -30,9 +31,20 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Host-side fault injection (gpp_diag_inject_cuda_failure): a countdown of checked CUDA
+// calls on this host thread; the call at which it reaches zero reports failure after it has
+// been made.
+thread_local int g_inject_countdown = 0;
+thread_local bool g_injected = false;
+
 int cuda_fail(cudaError_t e, const char* what) {
-  return fail(GPP_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  const bool inj = g_injected;
+  g_injected = false;
+  return fail(GPP_ERR_CUDA, "%s: %s (%s)%s", what, cudaGetErrorName(e), cudaGetErrorString(e),
+              inj ? " [injected by gpp_diag_inject_cuda_failure]" : "");
 }
+
+cudaError_t checked(cudaError_t e) { return gpp::checked(e); }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -103,10 +115,8 @@ int check_pointers(const gpp_problem& p, int precision, bool outputs = true) {
     if (!r.ptr) return fail(GPP_ERR_NULL_PTR, "%s is NULL", r.name);
     if (!aligned(r.ptr, r.align)) return fail(GPP_ERR_NULL_PTR, "%s is not %zu-byte aligned", r.name, r.align);
   }
-  if (precision == GPP_FP32_BULK) {
-    if (!p.aqsntemp_c64) return fail(GPP_ERR_NULL_PTR, "aqsntemp_c64 is NULL (GPP_FP32_BULK)");
-    if (!aligned(p.aqsntemp_c64, 8)) return fail(GPP_ERR_NULL_PTR, "aqsntemp_c64 is not 8-byte aligned");
-  }
+  if (precision == GPP_FP32_BULK && p.aqsntemp_c64 && !aligned(p.aqsntemp_c64, 8))
+    return fail(GPP_ERR_NULL_PTR, "aqsntemp_c64 is not 8-byte aligned");
   return GPP_OK;
 }
 
@@ -138,15 +148,21 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
   off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(double));
   if (f32) {
     pl.off_bt32 = off;
-    off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.nw * 32);
+    off = gpp::align_up(off + static_cast<size_t>(p.number_bands) *
+                                  (2 * ((p.nw + 4) / 4) + p.nw) * 16);  // f32_band_quads
     pl.off_am32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(float));
+    if (!p.aqsntemp_c64) {  // the library makes the complex64 copy of aqsntemp
+      pl.convert_c64 = true;
+      pl.off_aqsn32 = off;
+      off = gpp::align_up(off + static_cast<size_t>(p.number_bands) * p.ncouls * 2 * sizeof(float));
+    }
   }
   pl.gather_total = off;
   if (!gather_only) {
     int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = checked(cudaGetDevice(&dev));
+    if (e == cudaSuccess) e = checked(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (e == cudaSuccess) e = gpp::batched_prepare(pl.threads, pl.nw, f32, pl.igpt);
     if (e != cudaSuccess) return cuda_fail(e, "querying the device");
     int bps = o.blocks_per_sm ? o.blocks_per_sm
@@ -189,13 +205,15 @@ gpp::BatchInst describe(const gpp_problem& p, const gpp_options& o, bool f32,
   d.P = p.ngpown;
   d.n_ig_tiles = pl.n_ig_tiles;
   d.aqsn = reinterpret_cast<const double2*>(p.aqsntemp);
-  d.aqsn32 = f32 ? reinterpret_cast<const float2*>(p.aqsntemp_c64) : nullptr;
+  d.aqsn32 = !f32            ? nullptr
+             : pl.convert_c64 ? reinterpret_cast<const float2*>(ws + pl.off_aqsn32)
+                              : reinterpret_cast<const float2*>(p.aqsntemp_c64);
   d.eps = reinterpret_cast<const double2*>(p.I_eps_array);
   d.wt = reinterpret_cast<const double2*>(p.wtilde_array);
   d.am = reinterpret_cast<const double2*>(ws + pl.off_am);
   d.am32 = f32 ? reinterpret_cast<const float2*>(ws + pl.off_am32) : nullptr;
   d.bt = reinterpret_cast<const gpp::BandEntry*>(ws + pl.off_bt);
-  d.bt32 = f32 ? reinterpret_cast<const gpp::BandEntry32*>(ws + pl.off_bt32) : nullptr;
+  d.bt32 = f32 ? reinterpret_cast<const float4*>(ws + pl.off_bt32) : nullptr;
   d.colg = reinterpret_cast<const int*>(ws + pl.off_colvalid);
   d.flags = reinterpret_cast<const int*>(ws + pl.off_flags);
   d.ach = p.achtemp;
@@ -222,8 +240,8 @@ int make_bwd_plan(const gpp_problem& p, const gpp_options& o, gpp::BwdPlan* plan
     return GPP_OK;
   }
   int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = checked(cudaGetDevice(&dev));
+  if (e == cudaSuccess) e = checked(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (e != cudaSuccess) return cuda_fail(e, "querying the device");
   const int bps = gpp::bwd_blocks_per_sm(static_cast<int>(p.nw));
   if (bps <= 0) return fail(GPP_ERR_CUDA, "occupancy query failed for the adjoint kernel");
@@ -261,8 +279,27 @@ int validate(const gpp_problem* prob, const gpp_options* opt, gpp_options* o) {
 }  // namespace
 
 namespace gpp {
+cudaError_t checked(cudaError_t e) {
+  if (g_inject_countdown > 0 && --g_inject_countdown == 0 && e == cudaSuccess) {
+    g_injected = true;
+    return cudaErrorUnknown;
+  }
+  return e;
+}
+
 int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
 void clear_error() { g_last_error.clear(); }
+
+int sigma_workspace_query(const gpp_problem* prob, const gpp_options* opt, size_t* bytes) {
+  *bytes = 0;
+  gpp_options o;
+  int rc = validate(prob, opt, &o);
+  if (rc) return rc;
+  gpp::FwdPlan plan;
+  if ((rc = make_plan(*prob, o, &plan))) return rc;
+  *bytes = plan.total;
+  return GPP_OK;
+}
 }  // namespace gpp
 
 extern "C" {
@@ -272,6 +309,26 @@ void gpp_options_default(gpp_options* opt) {
 }
 
 const char* gpp_last_error(void) { return g_last_error.c_str(); }
+
+int gpp_convert_c64(const gpp_c128* src, gpp_c64* dst, int64_t n, void* stream) {
+  if (n < 0) return fail(GPP_ERR_BAD_SIZE, "n %lld is negative", (long long)n);
+  if (n == 0) {
+    g_last_error.clear();
+    return GPP_OK;
+  }
+  if (!src || !dst) return fail(GPP_ERR_NULL_PTR, "src and dst must be non-NULL");
+  if (!aligned(src, 16) || !aligned(dst, 8))
+    return fail(GPP_ERR_NULL_PTR, "src must be 16-byte and dst 8-byte aligned");
+  cudaError_t e = checked(gpp::launch_convert_c64(src, n, dst, n, 1, 0, n, static_cast<cudaStream_t>(stream)));
+  if (e != cudaSuccess) return cuda_fail(e, "launching the complex64 conversion");
+  g_last_error.clear();
+  return GPP_OK;
+}
+
+void gpp_diag_inject_cuda_failure(int n) {
+  g_inject_countdown = n > 0 ? n : 0;
+  g_injected = false;
+}
 
 const char* gpp_version(void) { return "libgpp 0.1 (sm_103a)"; }
 
@@ -293,8 +350,8 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
   if ((rc = check_pointers(p, o.precision))) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (degenerate(p)) {
-    cudaError_t e = cudaMemsetAsync(p.achtemp, 0, p.nw * sizeof(gpp_c128), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.asxtemp, 0, p.nw * sizeof(gpp_c128), s);
+    cudaError_t e = checked(cudaMemsetAsync(p.achtemp, 0, p.nw * sizeof(gpp_c128), s));
+    if (e == cudaSuccess) e = checked(cudaMemsetAsync(p.asxtemp, 0, p.nw * sizeof(gpp_c128), s));
     if (e != cudaSuccess) return cuda_fail(e, "zeroing the outputs");
     g_last_error.clear();
     return GPP_OK;
@@ -314,32 +371,32 @@ int gpp_sigma(const gpp_problem* prob, const gpp_options* opt, void* workspace,
   gpp::BatchInst desc = describe(p, o, f32, plan, ws);
   desc.tile0 = 0;
   desc.tile_end = plan.ntiles;
-  cudaError_t e = mark(0);
+  cudaError_t e = checked(mark(0));
   if (e != cudaSuccess) return cuda_fail(e, "recording stage event 0");
-  e = gpp::launch_prep(p, plan, ws, f32, &desc, s);
+  e = checked(gpp::launch_prep(p, plan, ws, f32, &desc, s));
   if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
   if (o.debug_checks) {
     int flags[4];
-    e = cudaMemcpyAsync(flags, ws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    e = checked(cudaMemcpyAsync(flags, ws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    if (e == cudaSuccess) e = checked(cudaStreamSynchronize(s));
     if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
     if (flags[1] > 0)
       return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
                   flags[1]);
   }
-  if ((e = mark(1)) != cudaSuccess) return cuda_fail(e, "recording stage event 1");
+  if ((e = checked(mark(1))) != cudaSuccess) return cuda_fail(e, "recording stage event 1");
   const gpp::BatchInst* dptr = reinterpret_cast<const gpp::BatchInst*>(ws + plan.off_desc);
   double* partials = reinterpret_cast<double*>(ws + plan.off_partials);
-  e = gpp::launch_batched_main(dptr, 1, plan.ntiles, plan.nw, f32, plan.grid, plan.threads,
+  e = checked(gpp::launch_batched_main(dptr, 1, plan.ntiles, plan.nw, f32, plan.grid, plan.threads,
                                plan.igpt, reinterpret_cast<unsigned long long*>(ws + plan.off_counter),
-                               partials, s);
+                               partials, s));
   if (e != cudaSuccess) return cuda_fail(e, "launching the main sum");
-  if ((e = mark(2)) != cudaSuccess) return cuda_fail(e, "recording stage event 2");
-  e = gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s);
+  if ((e = checked(mark(2))) != cudaSuccess) return cuda_fail(e, "recording stage event 2");
+  e = checked(gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s));
   if (e != cudaSuccess) return cuda_fail(e, "launching the final reduction");
-  if ((e = mark(3)) != cudaSuccess) return cuda_fail(e, "recording stage event 3");
+  if ((e = checked(mark(3))) != cudaSuccess) return cuda_fail(e, "recording stage event 3");
   if (o.debug_checks) {
-    e = cudaStreamSynchronize(s);
+    e = checked(cudaStreamSynchronize(s));
     if (e != cudaSuccess) return cuda_fail(e, "running the sum");
   }
   g_last_error.clear();
@@ -378,7 +435,7 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
     size_t sizes[4] = {pg, pg, bg, bg};
     for (int i = 0; i < 4; ++i)
       if (outs[i] && sizes[i]) {
-        cudaError_t e = cudaMemsetAsync(outs[i], 0, sizes[i], s);
+        cudaError_t e = checked(cudaMemsetAsync(outs[i], 0, sizes[i], s));
         if (e != cudaSuccess) return cuda_fail(e, "zeroing gradients");
       }
     g_last_error.clear();
@@ -390,19 +447,19 @@ int gpp_sigma_backward(const gpp_problem* prob, const gpp_options* opt,
     return fail(GPP_ERR_WORKSPACE, "adjoint workspace must be 256-byte aligned with %zu bytes",
                 plan.total);
   char* ws = static_cast<char*>(workspace);
-  cudaError_t e = gpp::launch_prep(p, plan.fwd, ws, false, nullptr, s);
+  cudaError_t e = checked(gpp::launch_prep(p, plan.fwd, ws, false, nullptr, s));
   if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
   if (o.debug_checks) {
     int flags[4];
-    e = cudaMemcpyAsync(flags, ws + plan.fwd.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    e = checked(cudaMemcpyAsync(flags, ws + plan.fwd.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    if (e == cudaSuccess) e = checked(cudaStreamSynchronize(s));
     if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
     if (flags[1] > 0)
       return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
                   flags[1]);
   }
-  e = gpp::launch_bwd(p, o.occ_mode, ach_scale(o), sexcut2(o), plan, ws, grad_achtemp,
-                      grad_asxtemp, *grads, s);
+  e = checked(gpp::launch_bwd(p, o.occ_mode, ach_scale(o), sexcut2(o), plan, ws, grad_achtemp,
+                      grad_asxtemp, *grads, s));
   if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint kernels");
   g_last_error.clear();
   return GPP_OK;
@@ -441,8 +498,8 @@ int batched_layout(const gpp_problem* probs, int n, const gpp_options* opt, bool
   bp->threads = o.block_threads ? o.block_threads : 128;
   bp->igpt = o.ig_per_thread ? o.ig_per_thread : kDefaultIgpt;
   int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = checked(cudaGetDevice(&dev));
+  if (e == cudaSuccess) e = checked(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (e == cudaSuccess) e = gpp::batched_prepare(bp->threads, bp->nw, bp->f32, bp->igpt);
   if (e != cudaSuccess) return cuda_fail(e, "querying the device");
   int bps = o.blocks_per_sm ? o.blocks_per_sm
@@ -515,16 +572,16 @@ int batched_bind(gpp_batched_plan* bp, void* workspace, size_t bytes) {
 
 cudaError_t batched_enqueue(gpp_batched_plan* bp, cudaStream_t s) {
   for (int i = 0; i < bp->n; ++i) {
-    cudaError_t e = gpp::launch_prep(bp->probs[i], bp->iplan[i], bp->ws + bp->ioff[i], bp->f32,
-                                     nullptr, s);
+    cudaError_t e = checked(gpp::launch_prep(bp->probs[i], bp->iplan[i], bp->ws + bp->ioff[i], bp->f32,
+                                     nullptr, s));
     if (e != cudaSuccess) return e;
   }
   const auto* inst = reinterpret_cast<const gpp::BatchInst*>(bp->ws + bp->off_inst);
   double* partials = reinterpret_cast<double*>(bp->ws + bp->off_partials);
-  cudaError_t e = gpp::launch_batched_main(inst, bp->n, bp->ntiles, bp->nw, bp->f32, bp->grid,
+  cudaError_t e = checked(gpp::launch_batched_main(inst, bp->n, bp->ntiles, bp->nw, bp->f32, bp->grid,
                                            bp->threads, bp->igpt,
                                            reinterpret_cast<unsigned long long*>(bp->ws + bp->off_counter),
-                                           partials, s);
+                                           partials, s));
   if (e != cudaSuccess) return e;
   return gpp::launch_batched_reduce(inst, bp->n, bp->nw, bp->f32, partials, s);
 }
@@ -551,9 +608,9 @@ int gpp_batched_plan_create(gpp_batched_plan** plan, const gpp_problem* probs, i
     return rc;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(bp->ws + bp->off_inst, bp->inst.data(),
-                                  bp->inst.size() * sizeof(gpp::BatchInst), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t e = checked(cudaMemcpyAsync(bp->ws + bp->off_inst, bp->inst.data(),
+                                  bp->inst.size() * sizeof(gpp::BatchInst), cudaMemcpyHostToDevice, s));
+  if (e == cudaSuccess) e = checked(cudaStreamSynchronize(s));
   if (e != cudaSuccess) {
     delete bp;
     return cuda_fail(e, "uploading the instance descriptors");
@@ -562,16 +619,18 @@ int gpp_batched_plan_create(gpp_batched_plan** plan, const gpp_problem* probs, i
     // Captured on a private stream (the caller's may be the legacy default stream, which
     // cannot be captured); the graph is later launched on the caller's stream.
     cudaStream_t cs = nullptr;
-    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    e = checked(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // (a capture that has begun is always ended, whatever fails inside it)
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t e2 = batched_enqueue(bp, cs);
-      e = cudaStreamEndCapture(cs, &bp->graph);
+      cudaError_t e2 = checked(batched_enqueue(bp, cs));
+      e = checked(cudaStreamEndCapture(cs, &bp->graph));
       if (e2 != cudaSuccess) e = e2;
     }
     if (cs) cudaStreamDestroy(cs);
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&bp->exec, bp->graph, 0);
+    if (e == cudaSuccess) e = checked(cudaGraphInstantiate(&bp->exec, bp->graph, 0));
     if (e != cudaSuccess) {
+      if (bp->exec) cudaGraphExecDestroy(bp->exec);
       if (bp->graph) cudaGraphDestroy(bp->graph);
       delete bp;
       return cuda_fail(e, "capturing the batched graph");
@@ -585,7 +644,7 @@ int gpp_batched_plan_create(gpp_batched_plan** plan, const gpp_problem* probs, i
 int gpp_batched_plan_run(gpp_batched_plan* plan, void* stream) {
   if (!plan) return fail(GPP_ERR_NULL_PTR, "plan is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = plan->exec ? cudaGraphLaunch(plan->exec, s) : batched_enqueue(plan, s);
+  cudaError_t e = checked(plan->exec ? cudaGraphLaunch(plan->exec, s) : batched_enqueue(plan, s));
   if (e != cudaSuccess) return cuda_fail(e, "running the batch");
   g_last_error.clear();
   return GPP_OK;
@@ -642,6 +701,16 @@ void host_layout(const gpp_problem& p, int precision, size_t sigma_bytes, HostLa
   L->total = gpp::align_up(off + sigma_bytes);
 }
 
+// The problem whose plan the host path uses: in FP32-bulk the host path always holds a
+// device complex64 copy of aqsntemp (segment 8), copied from the caller's or converted chunk
+// by chunk on the device, so the sum itself never converts.
+gpp_problem host_sum_problem(const gpp_problem& h, int precision) {
+  gpp_problem q = h;
+  if (precision == GPP_FP32_BULK && !q.aqsntemp_c64)
+    q.aqsntemp_c64 = reinterpret_cast<const gpp_c64*>(h.aqsntemp);  // stands for segment 8
+  return q;
+}
+
 // Two streams per device for the host entry point, created on first use and kept for the
 // life of the process: one for the host-to-device copies, one for every other chunk of the
 // main sum (so that a chunk's last wave overlaps the next chunk's first).
@@ -654,15 +723,15 @@ std::vector<HostStreams> g_host_streams;
 
 cudaError_t host_streams(HostStreams* out) {
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = checked(cudaGetDevice(&dev));
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_host_streams_mu);
   if (static_cast<int>(g_host_streams.size()) <= dev) g_host_streams.resize(dev + 1);
   HostStreams& hs = g_host_streams[dev];
-  if (!hs.copy && (e = cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking)) != cudaSuccess)
+  if (!hs.copy && (e = checked(cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking))) != cudaSuccess)
     return e;
   if (!hs.compute &&
-      (e = cudaStreamCreateWithFlags(&hs.compute, cudaStreamNonBlocking)) != cudaSuccess)
+      (e = checked(cudaStreamCreateWithFlags(&hs.compute, cudaStreamNonBlocking))) != cudaSuccess)
     return e;
   *out = hs;
   return cudaSuccess;
@@ -674,7 +743,7 @@ struct EventSet {
   cudaError_t make(int n) {
     ev.assign(n, nullptr);
     for (auto& x : ev) {
-      cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      cudaError_t e = checked(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -691,7 +760,7 @@ size_t gpp_sigma_host_workspace_size(const gpp_problem* prob, const gpp_options*
   gpp_options o;
   if (validate(prob, opt, &o)) return 0;
   gpp::FwdPlan plan;
-  if (make_plan(*prob, o, &plan)) return 0;
+  if (make_plan(host_sum_problem(*prob, o.precision), o, &plan)) return 0;
   HostLayout L;
   host_layout(*prob, o.precision, plan.total, &L);
   g_last_error.clear();
@@ -706,7 +775,7 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   const gpp_problem& h = *prob;
   if ((rc = check_pointers(h, o.precision))) return rc;
   gpp::FwdPlan plan;
-  if ((rc = make_plan(h, o, &plan))) return rc;
+  if ((rc = make_plan(host_sum_problem(h, o.precision), o, &plan))) return rc;
   HostLayout L;
   host_layout(h, o.precision, plan.total, &L);
   if (!workspace || !aligned(workspace, gpp::kAlign) || workspace_bytes < L.total)
@@ -715,7 +784,7 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t W = h.nw;
   if (degenerate(h)) {
-    cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = checked(cudaStreamSynchronize(s));
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the stream");
     memset(h.achtemp, 0, W * sizeof(gpp_c128));
     memset(h.asxtemp, 0, W * sizeof(gpp_c128));
@@ -750,11 +819,11 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
                                             std::max(1.0, (2.0 * P + B) * G * 16 / chunk_bytes)));
   K = static_cast<int>(std::min<int64_t>(K, nigt));
   HostStreams hs;
-  cudaError_t e = host_streams(&hs);
+  cudaError_t e = checked(host_streams(&hs));
   EventSet ev;
   // [0] start, [1] common inputs copied, [2] gather done, [3 .. 3+K) chunk k copied,
   // [3+K] last chunk on the second stream done
-  if (e == cudaSuccess) e = ev.make(4 + K);
+  if (e == cudaSuccess) e = checked(ev.make(4 + K));
   if (e != cudaSuccess) return cuda_fail(e, "creating the host path's streams and events");
   const int64_t tile_ig = static_cast<int64_t>(plan.threads) * plan.igpt;
   auto h2d = [&](size_t seg, const void* src, size_t bytes) {
@@ -766,15 +835,27 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
                              static_cast<const char*>(src) + c0 * esize, G * esize,
                              (c1 - c0) * esize, rows, cudaMemcpyHostToDevice, hs.copy);
   };
-  e = cudaEventRecord(ev.ev[0], s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.copy, ev.ev[0], 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.compute, ev.ev[0], 0);
-  if (e == cudaSuccess) e = h2d(0, h.aqsmtemp, B * G * 16);
-  if (e == cudaSuccess) e = h2d(4, h.vcoul, G * 8);
-  if (e == cudaSuccess) e = h2d(5, h.inv_igp_index, P * 4);
-  if (e == cudaSuccess) e = h2d(6, h.indinv, (G + 1) * 4);
-  if (e == cudaSuccess) e = h2d(7, h.wx_array, B * W * 8);
-  if (e == cudaSuccess) e = cudaEventRecord(ev.ev[1], hs.copy);
+  // After the first copy is enqueued, an error return first waits for the work already
+  // enqueued on the three streams: the copies read the caller's host arrays and write the
+  // workspace, which the caller may free as soon as the call returns.
+  auto drain = [&]() {
+    cudaStreamSynchronize(hs.copy);
+    cudaStreamSynchronize(hs.compute);
+    cudaStreamSynchronize(s);
+  };
+  auto drain_fail = [&](cudaError_t err, const char* what) {
+    drain();
+    return cuda_fail(err, what);
+  };
+  e = checked(cudaEventRecord(ev.ev[0], s));
+  if (e == cudaSuccess) e = checked(cudaStreamWaitEvent(hs.copy, ev.ev[0], 0));
+  if (e == cudaSuccess) e = checked(cudaStreamWaitEvent(hs.compute, ev.ev[0], 0));
+  if (e == cudaSuccess) e = checked(h2d(0, h.aqsmtemp, B * G * 16));
+  if (e == cudaSuccess) e = checked(h2d(4, h.vcoul, G * 8));
+  if (e == cudaSuccess) e = checked(h2d(5, h.inv_igp_index, P * 4));
+  if (e == cudaSuccess) e = checked(h2d(6, h.indinv, (G + 1) * 4));
+  if (e == cudaSuccess) e = checked(h2d(7, h.wx_array, B * W * 8));
+  if (e == cudaSuccess) e = checked(cudaEventRecord(ev.ev[1], hs.copy));
   // Chunk sizes double (boundaries at nigt (2^k - 1) / (2^K - 1), each chunk at least one
   // G-vector tile): the sum starts after a small first chunk has arrived, and every later
   // chunk arrives while the ones before it are summed.
@@ -787,13 +868,19 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   }
   for (int k = 0; k < K && e == cudaSuccess; ++k) {
     const int64_t c0 = igt0[k] * tile_ig, c1 = std::min<int64_t>(igt0[k + 1] * tile_ig, G);
-    e = h2d_cols(1, h.aqsntemp, 16, B, c0, c1);
-    if (e == cudaSuccess && f32) e = h2d_cols(8, h.aqsntemp_c64, 8, B, c0, c1);
-    if (e == cudaSuccess) e = h2d_cols(2, h.I_eps_array, 16, P, c0, c1);
-    if (e == cudaSuccess) e = h2d_cols(3, h.wtilde_array, 16, P, c0, c1);
-    if (e == cudaSuccess) e = cudaEventRecord(ev.ev[3 + k], hs.copy);
+    e = checked(h2d_cols(1, h.aqsntemp, 16, B, c0, c1));
+    if (e == cudaSuccess && f32) {
+      if (h.aqsntemp_c64)
+        e = checked(h2d_cols(8, h.aqsntemp_c64, 8, B, c0, c1));
+      else  // converted on the device from the chunk just copied, in copy-stream order
+        e = checked(gpp::launch_convert_c64(d.aqsntemp, G, const_cast<gpp_c64*>(d.aqsntemp_c64), G, B,
+                                    c0, c1, hs.copy));
+    }
+    if (e == cudaSuccess) e = checked(h2d_cols(2, h.I_eps_array, 16, P, c0, c1));
+    if (e == cudaSuccess) e = checked(h2d_cols(3, h.wtilde_array, 16, P, c0, c1));
+    if (e == cudaSuccess) e = checked(cudaEventRecord(ev.ev[3 + k], hs.copy));
   }
-  if (e != cudaSuccess) return cuda_fail(e, "copying inputs to the device");
+  if (e != cudaSuccess) return drain_fail(e, "copying inputs to the device");
 
   cudaEvent_t stage[4] = {nullptr, nullptr, nullptr, nullptr};
   if (o.stage_events)
@@ -804,23 +891,25 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
   gpp::BatchInst desc = describe(d, o, f32, plan, sws);
   desc.tile0 = 0;
   desc.tile_end = plan.ntiles;
-  e = cudaStreamWaitEvent(s, ev.ev[1], 0);
-  if (e == cudaSuccess) e = mark(0);
-  if (e == cudaSuccess) e = gpp::launch_prep(d, plan, sws, f32, &desc, s);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  e = checked(cudaStreamWaitEvent(s, ev.ev[1], 0));
+  if (e == cudaSuccess) e = checked(mark(0));
+  if (e == cudaSuccess) e = checked(gpp::launch_prep(d, plan, sws, f32, &desc, s));
+  if (e != cudaSuccess) return drain_fail(e, "launching the column gather");
   if (o.debug_checks) {
     int flags[4];
-    e = cudaMemcpyAsync(flags, sws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "reading the index checks");
-    if (flags[1] > 0)
+    e = checked(cudaMemcpyAsync(flags, sws + plan.off_flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    if (e == cudaSuccess) e = checked(cudaStreamSynchronize(s));
+    if (e != cudaSuccess) return drain_fail(e, "reading the index checks");
+    if (flags[1] > 0) {
+      drain();
       return fail(GPP_ERR_BAD_INDEX, "%d inv_igp_index / indinv entries are outside [0, ncouls]",
                   flags[1]);
+    }
   }
-  e = cudaEventRecord(ev.ev[2], s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(hs.compute, ev.ev[2], 0);
-  if (e == cudaSuccess) e = mark(1);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the column gather");
+  e = checked(cudaEventRecord(ev.ev[2], s));
+  if (e == cudaSuccess) e = checked(cudaStreamWaitEvent(hs.compute, ev.ev[2], 0));
+  if (e == cudaSuccess) e = checked(mark(1));
+  if (e != cudaSuccess) return drain_fail(e, "launching the column gather");
   const gpp::BatchInst* dptr = reinterpret_cast<const gpp::BatchInst*>(sws + plan.off_desc);
   double* partials = reinterpret_cast<double*>(sws + plan.off_partials);
   auto* counters = reinterpret_cast<unsigned long long*>(ws + L.off_counters);
@@ -829,24 +918,24 @@ int gpp_sigma_host(const gpp_problem* prob, const gpp_options* opt, void* worksp
     cudaStream_t sk = (k & 1) ? hs.compute : s;
     const int64_t t0 = igt0[k] * static_cast<int64_t>(P), t1 = igt0[k + 1] * static_cast<int64_t>(P);
     const int grid = static_cast<int>(std::min<int64_t>(plan.grid, t1 - t0));
-    e = cudaStreamWaitEvent(sk, ev.ev[3 + k], 0);
+    e = checked(cudaStreamWaitEvent(sk, ev.ev[3 + k], 0));
     if (e == cudaSuccess)
-      e = gpp::launch_batched_main(dptr, 1, t1, plan.nw, f32, grid, plan.threads, plan.igpt,
-                                   counters + k, partials, sk, t0);
+      e = checked(gpp::launch_batched_main(dptr, 1, t1, plan.nw, f32, grid, plan.threads, plan.igpt,
+                                   counters + k, partials, sk, t0));
     second_used = second_used || (k & 1);
   }
   if (e == cudaSuccess && second_used) {
-    e = cudaEventRecord(ev.ev[3 + K], hs.compute);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev.ev[3 + K], 0);
+    e = checked(cudaEventRecord(ev.ev[3 + K], hs.compute));
+    if (e == cudaSuccess) e = checked(cudaStreamWaitEvent(s, ev.ev[3 + K], 0));
   }
-  if (e == cudaSuccess) e = mark(2);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the main sum");
-  e = gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s);
-  if (e == cudaSuccess) e = mark(3);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.achtemp, d.achtemp, W * 16, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.asxtemp, d.asxtemp, W * 16, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "running the sum and copying the outputs back");
+  if (e == cudaSuccess) e = checked(mark(2));
+  if (e != cudaSuccess) return drain_fail(e, "launching the main sum");
+  e = checked(gpp::launch_batched_reduce(dptr, 1, plan.nw, f32, partials, s));
+  if (e == cudaSuccess) e = checked(mark(3));
+  if (e == cudaSuccess) e = checked(cudaMemcpyAsync(h.achtemp, d.achtemp, W * 16, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) e = checked(cudaMemcpyAsync(h.asxtemp, d.asxtemp, W * 16, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) e = checked(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) return drain_fail(e, "running the sum and copying the outputs back");
   g_last_error.clear();
   return GPP_OK;
 }

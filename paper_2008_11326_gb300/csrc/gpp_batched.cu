@@ -74,17 +74,18 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
                                                           double* __restrict__ partials) {
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
-  // FP32-bulk: the threads' compensated pairs, [2][4W][blockDim.x] floats, their FP64
-  // wtilde, double2[blockDim.x], the FP64 band table pointer [blockDim.x], I w as
-  // float2[blockDim.x], then the tile's
-  // G-vectors sorted by Re w (float keys and int positions, pow2_ceil(blockDim.x * igpt)
-  // each) (dynamic shared memory of batched_smem_bytes)
+  __shared__ const BandEntry* s_bt64;  // FP32-bulk: the FP64 band table, for the exact path
+  // FP32-bulk: the threads' slots (F32Slots: band and tile compensated pairs, FP64 wtilde;
+  // (16 W + 4) floats per thread), then the tile's G-vector positions in sorted order
+  // (int[pow2_ceil(blockDim.x * igpt)]); the sort keys (float, as many) alias the start of
+  // the slots, which are written only after the sort (dynamic shared memory of
+  // batched_smem_bytes)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  float* const s_pair = reinterpret_cast<float*>(dyn_smem);
+  float* const s_slots = reinterpret_cast<float*>(dyn_smem);
   const int tile_n = blockDim.x * igpt;
   const int sort_n = F32 ? pow2_ceil(tile_n) : 0;
-  float* const s_key = s_pair + (2 * 4 * W + 8) * blockDim.x;
-  int* const s_pos = reinterpret_cast<int*>(s_key + sort_n);
+  float* const s_key = s_slots;
+  int* const s_pos = reinterpret_cast<int*>(s_slots + F32Slots<W>::kFloats * blockDim.x);
   for (;;) {
     if (threadIdx.x == 0) s_t = t_begin + static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
@@ -111,8 +112,7 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) acc[k] = 0.0;
     if (F32) {
-#pragma unroll
-      for (int k = 0; k < 2 * 4 * W; ++k) s_pair[k * blockDim.x + threadIdx.x] = 0.0f;
+      if (threadIdx.x == 0) s_bt64 = d.bt;
       // With at least kSortBands bands, the G-vectors of each pass over the tile (blockDim.x
       // of them, when that is a power of two; else the whole tile) are taken in order of
       // Re w, so that the 32 of a warp (consecutive in that order) span a narrow range of
@@ -137,6 +137,10 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
         const int nt = blockDim.x;
         bitonic_sort(s_key, s_pos, sort_n, (nt & (nt - 1)) == 0 ? nt : sort_n);
       }
+      __syncthreads();  // the keys' space becomes the threads' slots
+#pragma unroll
+      for (int k = 0; k < 2 * W; ++k)
+        *F32Slots<W>::tile4(s_slots, k) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int j = 0; j < igpt; ++j) {
       // F32: a padding position (>= tile_n, key +inf like an inert one) can sort into the
@@ -145,52 +149,64 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
       const int64_t ig = F32 ? igt * tile_n + q : (igt * igpt + j) * blockDim.x + threadIdx.x;
       const bool live = (!F32 || q < tile_n) && ig < G && col_ok;
       double2 w = make_double2(0.5, 1.0);  // inert lane: finite terms, zero weight
-      double2 I = make_double2(0.0, 0.0);
-      if (live) {
-        w = ldg2(d.wt + p * G + ig);
-        I = ldg2(d.eps + p * G + ig);
-      }
+      if (live) w = ldg2(d.wt + p * G + ig);
       const double wabs2 = fma(w.x, w.x, w.y * w.y);
       const bool fast_lane = w.x >= 0.0 && gt_nonneg(wabs2, kFastWabs2Lo) &&
                              lt_nonneg(wabs2, kFastWabs2Hi);
       const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
-      if (F32) {
-        if (fast) {
-          band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32, d.bt,
-                           w, I, live, s_pair);
-        } else {  // the general path in FP64, folded into the pairs
-          double a[4 * W];
+      if (F32 && fast) {
+        band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32,
+                         &s_bt64, w, live, s_slots);
+        // I w in FP64 once per pair (w re-read from the thread's slot, I from memory, so
+        // that neither stays in registers through the band loop)
+        const volatile double* ws = reinterpret_cast<volatile double*>(F32Slots<W>::w64(s_slots));
+        const double2 wv = make_double2(ws[0], ws[1]);
+        double2 I = make_double2(0.0, 0.0);
+        if (live) I = ldg2(d.eps + p * G + ig);
+        fold_band_sums<W>(s_slots, make_double2(fma(I.x, wv.x, -I.y * wv.y),
+                                                fma(I.x, wv.y, I.y * wv.x)));
+        continue;
+      }
+      double2 I = make_double2(0.0, 0.0);
+      if (live) I = ldg2(d.eps + p * G + ig);
+      const double Iwr = fma(I.x, w.x, -I.y * w.y);
+      const double Iwi = fma(I.x, w.y, I.y * w.x);
+      if (F32) {  // the general path in FP64, folded into the tile pairs
+        double a[4 * W];
 #pragma unroll
-          for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
-          const double Iwr = fma(I.x, w.x, -I.y * w.y);
-          const double Iwi = fma(I.x, w.y, I.y * w.x);
-          band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                              w.x, w.y, Iwr, Iwi, d.sx2, a);
+        for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
+        band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                            w.x, w.y, Iwr, Iwi, d.sx2, a);
 #pragma unroll
-          for (int k = 0; k < 4 * W; ++k) {
-            const float h = static_cast<float>(a[k]);
-            float& ph = s_pair[k * blockDim.x + threadIdx.x];
-            float& pl = s_pair[(4 * W + k) * blockDim.x + threadIdx.x];
-            pair_add(ph, pl, h, static_cast<float>(a[k] - static_cast<double>(h)));
+        for (int qd = 0; qd < W; ++qd) {
+          float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double v = a[4 * qd + i];
+            const float h = static_cast<float>(v);
+            pair_add(quad_elem(th, i), quad_elem(tl, i), h, static_cast<float>(v - static_cast<double>(h)));
           }
+          *F32Slots<W>::tile4(s_slots, qd) = th;
+          *F32Slots<W>::tile4(s_slots, W + qd) = tl;
         }
+      } else if (fast) {
+        band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                           w.x, w.y, Iwr, Iwi, 0.0, acc);
       } else {
-        const double Iwr = fma(I.x, w.x, -I.y * w.y);
-        const double Iwi = fma(I.x, w.y, I.y * w.x);
-        if (fast)
-          band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                             w.x, w.y, Iwr, Iwi, 0.0, acc);
-        else
-          band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                              w.x, w.y, Iwr, Iwi, d.sx2, acc);
+        band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                            w.x, w.y, Iwr, Iwi, d.sx2, acc);
       }
     }
     if (F32) {
       float hi[4 * W], lo[4 * W];
 #pragma unroll
-      for (int k = 0; k < 4 * W; ++k) {
-        hi[k] = s_pair[k * blockDim.x + threadIdx.x];
-        lo[k] = s_pair[(4 * W + k) * blockDim.x + threadIdx.x];
+      for (int qd = 0; qd < W; ++qd) {
+        float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          hi[4 * qd + i] = quad_elem(th, i);
+          lo[4 * qd + i] = quad_elem(tl, i);
+        }
       }
       block_pairs<4 * W>(hi, lo, reinterpret_cast<float2*>(red),
                          reinterpret_cast<float2*>(partials) + t * 4 * W);
@@ -257,9 +273,10 @@ const void* batched_kernel_ptr(int nw, bool f32) {
 }  // namespace
 
 size_t batched_smem_bytes(int threads, int nw, bool f32, int igpt) {
-  return f32 ? static_cast<size_t>(threads) * (2 * 4 * nw * sizeof(float) + 2 * sizeof(double) +
-                                               sizeof(void*) + 2 * sizeof(float)) +
-                   static_cast<size_t>(pow2_ceil(threads * igpt)) * (sizeof(float) + sizeof(int))
+  // F32Slots<nw>::kFloats floats per thread, then the sorted positions (the keys alias the
+  // slots: pow2_ceil(threads * igpt) <= 16 threads <= 16 nw threads floats)
+  return f32 ? static_cast<size_t>(threads) * (16 * nw + 4) * sizeof(float) +
+                   static_cast<size_t>(pow2_ceil(threads * igpt)) * sizeof(int)
              : 0;
 }
 

@@ -23,6 +23,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gpp_device.cuh"
 #include "gpp_internal.h"
 #include "gpp_terms_f64.cuh"
@@ -59,7 +61,7 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
                                 const int32_t* __restrict__ inv,
                                 const int32_t* __restrict__ indinv,
                                 const double* __restrict__ wx, int* flags, int* colg,
-                                BandEntry* bt, double2* am, BandEntry32* bt32, float2* am32,
+                                BandEntry* bt, double2* am, float4* bt32, float2* am32,
                                 BatchInst* desc_out, const BatchInst desc) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -82,30 +84,74 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
     bt[i] = BandEntry{make_double2(x, x * x), make_double2(4.0 * x, -0.5 * x)};
     if (!(x >= 0.0)) flags[0] = 1;
     if (!(fabs(x) < kFp32MaxX)) flags[2] = 1;
-    if (bt32) {
+    if (bt32) {  // layout of f32_band_quads (gpp_device.cuh)
       const float xf = static_cast<float>(x);
-      const int64_t b0 = i / W;
-      float lo = __int_as_float(0x7f800000), hi = -lo;  // the band's range, rounded outwards
-      for (int k = 0; k < W; ++k) {
-        lo = fminf(lo, __double2float_rd(wx[b0 * W + k]));
-        hi = fmaxf(hi, __double2float_ru(wx[b0 * W + k]));
+      const int64_t b0 = i / W, iw = i - b0 * W;
+      const int nq = (W + 4) / 4;
+      float* fb = reinterpret_cast<float*>(bt32 + b0 * (2 * nq + W));
+      fb[iw] = xf;
+      fb[4 * nq + iw] = static_cast<float>(x - static_cast<double>(xf));
+      bt32[b0 * (2 * nq + W) + 2 * nq + iw] =
+          make_float4(__double2float_rd(x), __double2float_ru(x),
+                      kMarginScale * (fabsf(xf) + kMarginW), 0.0f);
+      if (iw == 0) {  // the band's frequency range, rounded outwards, and the padding
+        float lo = __int_as_float(0x7f800000), hi = -lo;
+        for (int k = 0; k < W; ++k) {
+          lo = fminf(lo, __double2float_rd(wx[b0 * W + k]));
+          hi = fmaxf(hi, __double2float_ru(wx[b0 * W + k]));
+        }
+        fb[W] = lo;
+        fb[4 * nq + W] = hi;
+        for (int k = W + 1; k < 4 * nq; ++k) fb[k] = fb[4 * nq + k] = 0.0f;
       }
-      BandEntry32 e;
-      e.a = make_float4(xf, static_cast<float>(x * x), 4.0f * xf, lo);
-      e.b = make_float4(__double2float_rd(x), __double2float_ru(x),
-                        kMarginScale * (fabsf(xf) + kMarginW), hi);
-      bt32[i] = e;
     }
   }
 }
 
+// Complex128 -> complex64 (round to nearest) over a block of rows x columns: the FP32-bulk
+// copy of aqsntemp when the caller passes none. A streaming copy (read 16 bytes, write 8 per
+// element), bound by HBM.
+__global__ void gpp_convert_c64_kernel(const double2* __restrict__ src, int64_t ld_src,
+                                       float2* __restrict__ dst, int64_t ld_dst, int64_t rows,
+                                       int64_t c0, int64_t ncols) {
+  const int64_t n = rows * ncols;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += stride) {
+    const int64_t r = i / ncols, c = c0 + (i - r * ncols);
+    const double2 v = __ldcs(src + r * ld_src + c);
+    __stcs(dst + r * ld_dst + c, make_float2(static_cast<float>(v.x), static_cast<float>(v.y)));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_convert_c64(const gpp_c128* src, int64_t ld_src, gpp_c64* dst, int64_t ld_dst,
+                               int64_t rows, int64_t c0, int64_t c1, cudaStream_t s) {
+  const int64_t n = rows * (c1 - c0);
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // a grid of whole waves (8 CTAs of 256 threads per SM), fewer for small copies
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, static_cast<int64_t>(sms) * 8);
+  gpp_convert_c64_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(
+      reinterpret_cast<const double2*>(src), ld_src, reinterpret_cast<float2*>(dst), ld_dst,
+      rows, c0, c1 - c0);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
                         const BatchInst* desc, cudaStream_t s) {
   int* flags = reinterpret_cast<int*>(ws + plan.off_flags);
   cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
   if (e != cudaSuccess) return e;
+  if (fp32 && plan.convert_c64) {
+    e = launch_convert_c64(p.aqsntemp, p.ncouls, reinterpret_cast<gpp_c64*>(ws + plan.off_aqsn32),
+                           p.ncouls, p.number_bands, 0, p.ncouls, s);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t work = p.ngpown * p.number_bands + p.number_bands * p.nw + p.ngpown;
   int64_t blocks = (work + 255) / 256;
   if (blocks < 1) blocks = 1;
@@ -115,7 +161,7 @@ cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, boo
       reinterpret_cast<const double2*>(p.aqsmtemp), p.vcoul, p.inv_igp_index, p.indinv,
       p.wx_array, flags, reinterpret_cast<int*>(ws + plan.off_colvalid),
       reinterpret_cast<BandEntry*>(ws + plan.off_bt), reinterpret_cast<double2*>(ws + plan.off_am),
-      fp32 ? reinterpret_cast<BandEntry32*>(ws + plan.off_bt32) : nullptr,
+      fp32 ? reinterpret_cast<float4*>(ws + plan.off_bt32) : nullptr,
       fp32 ? reinterpret_cast<float2*>(ws + plan.off_am32) : nullptr,
       desc ? reinterpret_cast<BatchInst*>(ws + plan.off_desc) : nullptr, desc ? *desc : BatchInst());
   return cudaGetLastError();

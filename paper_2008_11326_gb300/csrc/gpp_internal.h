@@ -10,7 +10,6 @@
 namespace gpp {
 
 struct BandEntry;
-struct BandEntry32;
 
 // Layout of the caller's workspace for one forward call. Every segment starts on a
 // 256-byte boundary. With `gather_only` (instances of a batched plan, the adjoint) the
@@ -26,8 +25,10 @@ struct FwdPlan {
   size_t off_colvalid = 0;// int32[P]: global column of each local column, or -1
   size_t off_bt = 0;      // band table BandEntry[B][W] = {x, x^2, 4x, -x/2}
   size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
-  size_t off_bt32 = 0;    // FP32-bulk only: BandEntry32[B][W]
+  size_t off_bt32 = 0;    // FP32-bulk only: float4[B][f32_band_quads(W)]
   size_t off_am32 = 0;    // FP32-bulk only: gathered weights c64[P][B]
+  size_t off_aqsn32 = 0;  // FP32-bulk without a caller's copy: complex64 aqsntemp [B][G]
+  bool convert_c64 = false;  // the gather launch writes that copy first
   size_t gather_total = 0;
   size_t off_desc = 0;    // the instance descriptor (BatchInst)
   size_t off_counter = 0; // tile counter
@@ -41,9 +42,14 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct BatchInst;
 
 // Column gather, band tables and index checks (one kernel); with `desc` it also writes the
-// single-instance descriptor to plan.off_desc.
+// single-instance descriptor to plan.off_desc. With plan.convert_c64 the complex64 copy of
+// aqsntemp is written to plan.off_aqsn32 first.
 cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
                         const BatchInst* desc, cudaStream_t s);
+// dst[r][c] = complex64(src[r][c]) (round to nearest) for rows [0, rows) and columns
+// [c0, c1); leading dimensions in elements.
+cudaError_t launch_convert_c64(const gpp_c128* src, int64_t ld_src, gpp_c64* dst, int64_t ld_dst,
+                               int64_t rows, int64_t c0, int64_t c1, cudaStream_t s);
 // Workspace of the adjoint: the forward's gather segments plus the batch partials.
 struct BwdPlan {
   FwdPlan fwd;             // flags, colvalid, band table, gathered weights
@@ -77,7 +83,7 @@ struct BatchInst {
   const double2* am = nullptr;
   const float2* am32 = nullptr;
   const BandEntry* bt = nullptr;
-  const BandEntry32* bt32 = nullptr;
+  const float4* bt32 = nullptr;
   const int* colg = nullptr;
   const int* flags = nullptr;
   gpp_c128* ach = nullptr;
@@ -98,6 +104,15 @@ cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles
 // Per-instance fixed-order sum of the tile partials into the outputs.
 cudaError_t launch_batched_reduce(const BatchInst* inst, int ninst, int nw, bool f32,
                                   const double* partials, cudaStream_t s);
+
+// gpp_sigma's workspace bytes for this problem and these options, with the status of the
+// validation (GPP_OK, or the code gpp_sigma would return for these arguments).
+int sigma_workspace_query(const gpp_problem* prob, const gpp_options* opt, size_t* bytes);
+
+// Every CUDA call whose status the entry points check passes through here: returns e, or
+// a simulated failure when gpp_diag_inject_cuda_failure's countdown on this host thread
+// reaches this call (the call itself has been made).
+cudaError_t checked(cudaError_t e);
 
 // Sets the thread-local message returned by gpp_last_error(); returns `code`.
 int report_error(int code, const char* msg);

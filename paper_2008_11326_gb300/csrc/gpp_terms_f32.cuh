@@ -1,27 +1,39 @@
 // The FP32-bulk per-band evaluation (GPP_FP32_BULK), used by the main kernel
 // (gpp_batched.cu).
 //
-// Same decomposition and algebra as the FP64 path (gpp_fwd.cu, gpp_terms_f64.cuh), with the per-term
-// complex arithmetic in FP32 on complex64 data: the band-indexed aqsntemp is read from
-// its complex64 copy and the gathered weights conj(aqsmtemp) vcoul are rounded once by
-// the gather kernel; wtilde and I_eps are read in FP64 once per (igp, ig) pair and rounded
-// in registers. FP64 is kept where FP32 would change the answer:
+// Same decomposition and algebra as the FP64 path (gpp_fwd.cu, gpp_terms_f64.cuh), with the
+// per-term complex arithmetic in FP32 on complex64 data: the band-indexed aqsntemp is read
+// from its complex64 copy and the gathered weights conj(aqsmtemp) vcoul are rounded once by
+// the gather kernel; wtilde and I_eps are read in FP64 once per (igp, ig) pair. FP64 (or
+// FP32 pairs carrying FP64 information) is kept where FP32 would change the answer or lose
+// accuracy that does not average out:
 //
 //  * Branch decisions. The branch taken at |wdiff|^2 = 1/4 is discontinuous, and FP32
-//    rounding of x and w moves |wdiff|^2 by ~1e-7: on the benchmark shape thousands of
-//    terms would switch branch, an error of order 1e-4 in the sums. The kernel therefore
-//    evaluates d = |wdiff|^2 - 1/4 in FP32 together with a bound m on its rounding error,
+//    rounding moves |wdiff|^2 by ~1e-7: on the benchmark shape thousands of terms would
+//    switch branch, an error of order 1e-4 in the sums. The kernel evaluates
+//    d = |wdiff|^2 - 1/4 in FP32 together with a bound m on its rounding error,
 //        m = 2^-20 (|x| + 252)  >=  2^-20 (|x| + |Re w| + 2)   (|Re w| < 250 on the fast path),
 //    which is at least three times the worst-case error of the FP32 value when |d| < 0.1
 //    and |x| < 1e4 (and larger |d| are always decided correctly). If |d| > m the FP32 sign
 //    of d is the FP64 decision; otherwise (a fraction ~1e-6 of the terms) the lane
 //    recomputes |wdiff|^2 in FP64 exactly as the FP64 kernel does. Every branch decision
 //    is therefore the FP64 kernel's.
+//  * The difference x - Re w. Rounding x and Re w to FP32 separately moves wdiff by up to
+//    2^-24 (|x| + |Re w|), which relative to |wdiff| (>= 1/2 on branch 1) is up to ~30
+//    FP32 units for the benchmark's frequencies, and the same rounding of x (once per band)
+//    or of Re w (once per G-vector) is shared by many terms. Both carry their FP32 residual
+//    (x = x_hi + x_lo from the band table, Re w = wr + wr_lo per thread), and
+//    Ar = (x_hi - wr) + (x_lo - wr_lo) is accurate to a few units of Ar itself. S = x + w
+//    and Re C = Ar Sr + (Im w)^2 (C = x^2 - w^2 = A S) are formed from Ar and Sr, without the
+//    cancellation of x^2 - Re w^2.
 //  * The pole |wdiff| -> 0. There the FP32 product |wdiff|^2 |x + w|^2 can underflow; for
 //    |wdiff|^2 < 2^-30 the branch-2 coefficient 1/|x + w|^2 is taken in FP64.
-//  * Accumulation. Terms are summed in FP32 over chunks of kChunk bands, chunk sums are
-//    added into compensated (Kahan) FP32 pairs, the pairs are folded into FP64 at the end
-//    of every tile, and the block and final reductions are FP64 (gpp_fwd.cu).
+//  * Accumulation. Terms are summed in FP32 over chunks of kChunk bands (the rounding error
+//    of a running FP32 sum grows with the number of terms in it), every chunk sum is added
+//    into a compensated (Kahan) FP32 pair, and once per (igp, ig) pair the pair is
+//    multiplied by I w in double-FP32 arithmetic (I w formed in FP64) and added into the
+//    thread's compensated tile sums; the block and final reductions are compensated pairs
+//    and FP64 (gpp_batched.cu).
 //  * Inputs outside the fast path's range (negative frequencies, Re w < 0, |w|^2 outside
 //    (1e-12, 62499), |x| >= 1e4) are evaluated by the FP64 general path for the whole warp.
 //
@@ -40,12 +52,18 @@
 
 namespace gpp {
 
-constexpr int kChunk = 32;            // bands summed in plain FP32 before a Kahan merge
+#ifndef GPP_F32_CHUNK
+#define GPP_F32_CHUNK 16
+#endif
+constexpr int kChunk = GPP_F32_CHUNK;  // bands summed in plain FP32 before a Kahan merge
 constexpr float kPoleA2 = 9.313225746154785e-10f;  // 2^-30
 
 __device__ __forceinline__ float rcp_approx_f32(float d) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d));
+#ifdef GPP_F32_RCP_NEWTON
+  y = fmaf(y, fmaf(-d, y, 1.0f), y);
+#endif
   return y;
 }
 
@@ -61,38 +79,45 @@ __device__ __forceinline__ float msel(unsigned m, float a, float b) {
 
 // Per-(igp, ig) constants of the FP32 path.
 struct PairF32 {
-  float wr, wi, wi2, mw2r, w2i;
+  float wr, wr_lo, wi, wi2, w2i;  // Re w = wr + wr_lo; Im w; (Im w)^2; Im w^2
   float lo, hi;  // the warp's interval [min Re w - 1/2, max Re w + 1/2], widened by 2^-20
 };
 
-// The thread's slots in the FP32 path's shared memory (layout in band_loop_f32): the
-// compensated pairs, the FP64 wtilde and the FP64 band table of the instance, the last two
-// read only on the rare exact-decision path (kept there rather than in registers).
+// The thread's slots in the FP32 path's dynamic shared memory: the band sums' compensated
+// pairs (4W hi values then 4W lo values), the tile sums' compensated pairs (likewise), each
+// stored as float4 with a stride of blockDim.x (a thread's four consecutive values in one
+// 16-byte access, conflict-free across a warp), then the thread's FP64 wtilde (double2),
+// read only on the rare exact-decision path and at the end of a pair's band loop. Kept here
+// rather than in registers, which bound the kernel's occupancy.
 template <int W>
 struct F32Slots {
-  static __device__ __forceinline__ float* pair(float* sp, int k) {
-    return sp + k * blockDim.x + threadIdx.x;
+  static constexpr int kFloats = 16 * W + 4;  // per thread
+  // band pairs: quads [0, W) hold hi[4q .. 4q + 3], quads [W, 2W) lo; tile pairs follow
+  static __device__ __forceinline__ float4* band4(float* sp, int q) {
+    return reinterpret_cast<float4*>(sp) + q * blockDim.x + threadIdx.x;
+  }
+  static __device__ __forceinline__ float4* tile4(float* sp, int q) {
+    return reinterpret_cast<float4*>(sp) + (2 * W + q) * blockDim.x + threadIdx.x;
   }
   static __device__ __forceinline__ double2* w64(float* sp) {
-    return reinterpret_cast<double2*>(sp + 2 * 4 * W * blockDim.x) + threadIdx.x;
-  }
-  static __device__ __forceinline__ const BandEntry** bt64(float* sp) {
-    return reinterpret_cast<const BandEntry**>(sp + 2 * 4 * W * blockDim.x + 4 * blockDim.x) +
-           threadIdx.x;
-  }
-  // I w of the thread's G-vector in FP32 (applied to the chunk sums only)
-  static __device__ __forceinline__ float2* iw(float* sp) {
-    return reinterpret_cast<float2*>(sp + 2 * 4 * W * blockDim.x + 6 * blockDim.x) + threadIdx.x;
+    return reinterpret_cast<double2*>(sp + 16 * W * blockDim.x) + threadIdx.x;
   }
 };
 
+__device__ __forceinline__ float& quad_elem(float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
 // Bands [b0, b1) into the chunk sums c. OCC (whether these bands enter asxtemp) is a
-// template parameter: a runtime flag in this loop body costs instructions.
+// template parameter: a runtime flag in this loop body costs instructions. `bt64` (the FP64
+// band table, for the rare exact path) is read from shared memory.
 template <int W, bool OCC>
 __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* __restrict__ an_ptr,
                                           const float2* __restrict__ am_ptr,
-                                          const BandEntry32* __restrict__ bt32, float* sp,
+                                          const float4* __restrict__ bt32,
+                                          const BandEntry* const* s_bt64, float* sp,
                                           const PairF32& q, float (&c)[4 * W]) {
+  constexpr int NQ = f32_half_quads(W), FB = f32_band_quads(W);
   if (b0 >= b1) return;
   // the next band's aqsntemp and weight are loaded one band ahead (their global-memory
   // latency is the kernel's main stall); inert lanes read a valid element, and their I = 0
@@ -107,56 +132,61 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
       an_next = ldgf2(an_ptr + static_cast<int64_t>(b + 1) * G);
       am_next = ldgf2(am_ptr + b + 1);
     }
-    // the band sums run on M = am an; band_loop_f32 multiplies them by I w (the same for
-    // every band) when it merges a chunk
+    // the band sums run on M = am an; the caller multiplies them by I w (the same for
+    // every band) once the pair's bands are done
     const float Kr = fmaf(am.x, an.x, -am.y * an.y);
     const float Ki = fmaf(am.x, an.y, am.y * an.x);
     const float Kwr = -Ki * q.wi, Kwi = Kr * q.wi;
     const float K2r = fmaf(Kr, q.wr, Kwr), K2i = fmaf(Ki, q.wr, Kwi);
     const float P1r = -K2i * q.w2i, P1i = K2r * q.w2i;
-    const BandEntry32* e = bt32 + static_cast<int64_t>(b) * W;
-    // branch 1 for every lane: K conj(A) / |A|^2 and K2 conj(C) / |C|^2
-    auto branch1 = [&](int iw, float x2, float S2, float r, float tr, float ti) {
+    const float4* e = bt32 + static_cast<int64_t>(b) * FB;
+    // the far-path block: x_hi[], the band's lowest frequency; x_lo[], its highest
+    float4 hq[NQ], lq[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      hq[k] = __ldg(&e[k]);
+      lq[k] = __ldg(&e[NQ + k]);
+    }
+    auto xh = [&](int i) -> float { return quad_elem(hq[i >> 2], i & 3); };
+    auto xl = [&](int i) -> float { return quad_elem(lq[i >> 2], i & 3); };
+    // branch 1 for every lane: M conj(A) / |A|^2 and M w conj(C) / |C|^2
+    auto branch1 = [&](int iw, float Ar, float Sr, float S2, float r, float tr, float ti) {
       const float a1 = S2 * r;
       c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
       c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
       if (OCC) {
-        const float Yr = x2 + q.mw2r;
+        const float Yr = fmaf(Ar, Sr, q.wi2);  // Re C = Ar Sr + (Im w)^2
         const float ur = fmaf(K2r, Yr, P1r);
         const float ui = fmaf(K2i, Yr, P1i);
         c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
         c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
       }
     };
-    // the band's frequency range (rounded outwards) rides in the first entry's a.w / b.w
-    const float4 e0a = __ldg(&e[0].a);
-    const float4 e0b = __ldg(&e[0].b);
-    if (e0a.w > q.hi || e0b.w < q.lo) {
+    if (xh(W) > q.hi || xl(W) < q.lo) {
       // every frequency of the band outside the warp's interval on the same side
 #pragma unroll
       for (int iw = 0; iw < W; ++iw) {
-        const float4 ea = iw == 0 ? e0a : __ldg(&e[iw].a);
-        const float Ar = ea.x - q.wr;
+        const float Ar = (xh(iw) - q.wr) + (xl(iw) - q.wr_lo);
+        const float Sr = xh(iw) + q.wr;
         const float A2 = fmaf(Ar, Ar, q.wi2);
-        const float S2 = fmaf(ea.z, q.wr, A2);
+        const float S2 = fmaf(Sr, Sr, q.wi2);
         const float r = rcp_approx_f32(A2 * S2);
-        branch1(iw, ea.y, S2, r, fmaf(Kr, Ar, Kwr), fmaf(Ki, Ar, Kwi));
+        branch1(iw, Ar, Sr, S2, r, fmaf(Kr, Ar, Kwr), fmaf(Ki, Ar, Kwi));
       }
       continue;
     }
 #pragma unroll
     for (int iw = 0; iw < W; ++iw) {
-      const float4 ea = iw == 0 ? e0a : __ldg(&e[iw].a);
-      const float4 eb = iw == 0 ? e0b : __ldg(&e[iw].b);
-      const float x = ea.x, x2 = ea.y, x4 = ea.z;
-      const float Ar = x - q.wr;
+      const float4 eb = __ldg(&e[2 * NQ + iw]);  // x rounded down, up, margin
+      const float Ar = (xh(iw) - q.wr) + (xl(iw) - q.wr_lo);
+      const float Sr = xh(iw) + q.wr;
       const float A2 = fmaf(Ar, Ar, q.wi2);
-      const float S2 = fmaf(x4, q.wr, A2);
+      const float S2 = fmaf(Sr, Sr, q.wi2);
       float r = rcp_approx_f32(A2 * S2);
       const float tr = fmaf(Kr, Ar, Kwr);
       const float ti = fmaf(Ki, Ar, Kwi);
       if (eb.x > q.hi || eb.y < q.lo) {  // x outside the warp's interval
-        branch1(iw, x2, S2, r, tr, ti);
+        branch1(iw, Ar, Sr, S2, r, tr, ti);
         continue;
       }
       float b2 = A2 * r;
@@ -166,7 +196,7 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
       const bool pole = A2 < kPoleA2;
       if (__any_sync(0xffffffffu, near || pole)) {
         if (near || pole) {
-          const BandEntry* bt64 = *F32Slots<W>::bt64(sp);
+          const BandEntry* bt64 = *s_bt64;
           const double x64 = __ldg(&bt64[static_cast<int64_t>(b) * W + iw].lo.x);
           const double2 w64 = *F32Slots<W>::w64(sp);
           const double wi2_64 = w64.y * w64.y;
@@ -187,10 +217,11 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
         c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
         c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
         if (OCC) {
-          // branch 2: K (-conj(S)/2) / |S|^2 = (Re K Yr - Im K Im w/2, Im K Yr + Re K Im w/2) b2
+          // branch 2: M (-conj(S)/2) / |S|^2 = (Re M Yr - Im M Im w/2, Im M Yr + Re M Im w/2) b2
+          // with Yr = -Sr/2
           const float wih = 0.5f * q.wi;
           const float coef = msel(m, r, b2);
-          const float Yr = msel(m, x2, -0.5f * x) + msel(m, q.mw2r, -0.5f * q.wr);
+          const float Yr = msel(m, fmaf(Ar, Sr, q.wi2), -0.5f * Sr);
           const float ur = fmaf(msel(m, K2r, Kr), Yr, msel(m, P1r, -Ki * wih));
           const float ui = fmaf(msel(m, K2i, Ki), Yr, msel(m, P1i, Kr * wih));
           c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
@@ -201,32 +232,26 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
   }
 }
 
-// All bands of one (igp, ig) pair into the thread's compensated FP32 pairs hi + lo, which
-// live in shared memory (`sp`, layout [2][4W][blockDim.x] floats, then the threads' FP64
-// wtilde as double2[blockDim.x], the FP64 band table pointer [blockDim.x] and I w as
-// float2[blockDim.x]: touched once per chunk, or only on the rare exact-decision path, they
-// would otherwise hold registers through the band loop, and the FP32 path is limited by
-// occupancy). Bands are summed in
-// FP32 over chunks of kChunk bands and every chunk sum is added to the pair with Kahan's
-// compensation.
+// All bands of one (igp, ig) pair: sum_b M F into the thread's band pairs (hi + lo, in
+// shared memory, layout in F32Slots), which the caller multiplies by I w. Bands are summed
+// in FP32 over chunks of kChunk bands and every chunk sum is added to the pair with Kahan's
+// compensation. The FP64 wtilde is stored in the thread's slot for the exact path.
 template <int W>
 __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
                                               const float2* __restrict__ an_ptr,
                                               const float2* __restrict__ am_ptr,
-                                              const BandEntry32* __restrict__ bt32,
-                                              const BandEntry* __restrict__ bt64,
-                                              double2 w64, double2 I64, bool live,
-                                              float* sp) {
+                                              const float4* __restrict__ bt32,
+                                              const BandEntry* const* s_bt64, double2 w64,
+                                              bool live, float* sp) {
   PairF32 q;
   q.wr = static_cast<float>(w64.x);
+  q.wr_lo = static_cast<float>(w64.x - static_cast<double>(q.wr));
   q.wi = static_cast<float>(w64.y);
-  const float Ir = static_cast<float>(I64.x), Ii = static_cast<float>(I64.y);
   q.wi2 = q.wi * q.wi;
-  q.mw2r = -fmaf(q.wr, q.wr, -q.wi2);   // -Re w^2
   q.w2i = 2.0f * q.wr * q.wi;           // Im w^2
-  *F32Slots<W>::iw(sp) = make_float2(fmaf(Ir, q.wr, -Ii * q.wi), fmaf(Ir, q.wi, Ii * q.wr));
   *F32Slots<W>::w64(sp) = w64;
-  *F32Slots<W>::bt64(sp) = bt64;
+#pragma unroll
+  for (int k = 0; k < 2 * W; ++k) *F32Slots<W>::band4(sp, k) = make_float4(0.f, 0.f, 0.f, 0.f);
   {  // the warp's Re w interval (inert lanes, whose I is 0, left out)
     constexpr double kHalf = 0.5 + 9.5367431640625e-07;  // 1/2 + 2^-20
     float lo = __double2float_rd(w64.x - kHalf), hi = __double2float_ru(w64.x + kHalf);
@@ -249,23 +274,74 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
     const int bend = min(b0 + kChunk, B);
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
-    bands_f32<W, true>(b0, bocc, static_cast<int>(G), an_ptr, am_ptr, bt32, sp, q, c);
+    bands_f32<W, true>(b0, bocc, static_cast<int>(G), an_ptr, am_ptr, bt32, s_bt64, sp, q, c);
     if (bocc < bend)
-      bands_f32<W, false>(bocc, bend, static_cast<int>(G), an_ptr, am_ptr, bt32, sp, q, c);
-    // the chunk sums times I w, merged into the pairs with Kahan's compensation (the pair
-    // holds the running sum as hi + lo)
-    const float2 Iw = *F32Slots<W>::iw(sp);
+      bands_f32<W, false>(bocc, bend, static_cast<int>(G), an_ptr, am_ptr, bt32, s_bt64, sp, q,
+                          c);
+    // the chunk sums merged into the band pairs with Kahan's compensation (the pair holds
+    // the running sum as hi + lo), four values per shared-memory access
 #pragma unroll
-    for (int k = 0; k < 4 * W; ++k) {
-      const float cr = c[k & ~1], ci = c[k | 1];
-      const float v = (k & 1) ? fmaf(Iw.x, ci, Iw.y * cr) : fmaf(Iw.x, cr, -Iw.y * ci);
-      float& hi = *F32Slots<W>::pair(sp, k);
-      float& lo = *F32Slots<W>::pair(sp, 4 * W + k);
-      const float y = v + lo;
-      const float t = hi + y;
-      lo = y - (t - hi);
-      hi = t;
+    for (int qd = 0; qd < W; ++qd) {
+      float4 h = *F32Slots<W>::band4(sp, qd), l = *F32Slots<W>::band4(sp, W + qd);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float& hi = quad_elem(h, i);
+        float& lo = quad_elem(l, i);
+        const float y = c[4 * qd + i] + lo;
+        const float t = hi + y;
+        lo = y - (t - hi);
+        hi = t;
+      }
+      *F32Slots<W>::band4(sp, qd) = h;
+      *F32Slots<W>::band4(sp, W + qd) = l;
     }
+  }
+}
+
+// (h, l) with h + l = a b exactly for FP32 a, b (no overflow or underflow): the product
+// and its rounding error from a fused multiply-add.
+__device__ __forceinline__ void two_prod(float a, float b, float& h, float& l) {
+  h = a * b;
+  l = fmaf(a, b, -h);
+}
+
+// Adds I w times the thread's band sums into its tile pairs, in double-FP32 arithmetic:
+// with I w = (ar + ar_l) + i (ai + ai_l) (FP32 pairs of the FP64 product) and each band
+// sum z = zh + zl, every real product is taken as its exact FP32 product plus the
+// first-order cross terms, and added into the tile pair with pair_add. Relative error of
+// order 2^-44 per value; FP32 operations only (the FP64 pipe is narrow). Values are laid
+// out as in the chunk sums: 4 iw + {Re ach, Im ach, Re asx, Im asx}, so quad iw holds the
+// two complex values of frequency iw.
+template <int W>
+__device__ __forceinline__ void fold_band_sums(float* sp, double2 Iw) {
+  const float ar = static_cast<float>(Iw.x), ai = static_cast<float>(Iw.y);
+  const float ar_l = static_cast<float>(Iw.x - static_cast<double>(ar));
+  const float ai_l = static_cast<float>(Iw.y - static_cast<double>(ai));
+#pragma unroll
+  for (int qd = 0; qd < W; ++qd) {
+    float4 zh = *F32Slots<W>::band4(sp, qd), zl = *F32Slots<W>::band4(sp, W + qd);
+    float4 th = *F32Slots<W>::tile4(sp, qd), tl = *F32Slots<W>::tile4(sp, W + qd);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {  // complex value (components 2v: re, 2v + 1: im)
+      const float zrh = quad_elem(zh, 2 * v), zrl = quad_elem(zl, 2 * v);
+      const float zih = quad_elem(zh, 2 * v + 1), zil = quad_elem(zl, 2 * v + 1);
+      // re = ar zr - ai zi,  im = ar zi + ai zr
+      float p[4], e[4];
+      two_prod(ar, zrh, p[0], e[0]);
+      two_prod(ai, zih, p[1], e[1]);
+      two_prod(ar, zih, p[2], e[2]);
+      two_prod(ai, zrh, p[3], e[3]);
+      e[0] = fmaf(ar, zrl, fmaf(ar_l, zrh, e[0]));
+      e[1] = fmaf(ai, zil, fmaf(ai_l, zih, e[1]));
+      e[2] = fmaf(ar, zil, fmaf(ar_l, zih, e[2]));
+      e[3] = fmaf(ai, zrl, fmaf(ai_l, zrh, e[3]));
+      pair_add(quad_elem(th, 2 * v), quad_elem(tl, 2 * v), p[0], e[0]);
+      pair_add(quad_elem(th, 2 * v), quad_elem(tl, 2 * v), -p[1], -e[1]);
+      pair_add(quad_elem(th, 2 * v + 1), quad_elem(tl, 2 * v + 1), p[2], e[2]);
+      pair_add(quad_elem(th, 2 * v + 1), quad_elem(tl, 2 * v + 1), p[3], e[3]);
+    }
+    *F32Slots<W>::tile4(sp, qd) = th;
+    *F32Slots<W>::tile4(sp, W + qd) = tl;
   }
 }
 

@@ -61,11 +61,22 @@ class DeviceProblem:
             dp.make_c64()
         return dp
 
-    def make_c64(self):
-        """The complex64 copy of aqsntemp that precision='fp32_bulk' reads per band."""
-        c = self.aqsntemp.to(torch.complex64)
-        if c.device.type == "cpu" and self.aqsntemp.is_pinned():
-            c = c.pin_memory()
+    def make_c64(self, stream: torch.cuda.Stream | None = None):
+        """The complex64 copy of aqsntemp that precision='fp32_bulk' reads per band, kept for
+        later calls (without it, each fp32_bulk call converts into its workspace). On the
+        device the library's conversion kernel makes it (enqueued on ``stream``); a host
+        problem's copy is made on the host (pinned if aqsntemp is)."""
+        src = self.aqsntemp
+        if src.device.type == "cpu":
+            c = src.to(torch.complex64)
+            self.aqsntemp_c64 = c.pin_memory() if src.is_pinned() else c
+            return self
+        src = src.contiguous()
+        c = torch.empty(src.shape, dtype=torch.complex64, device=src.device)
+        N.check(N.lib().gpp_convert_c64(ctypes.c_void_p(src.data_ptr()),
+                                        ctypes.c_void_p(c.data_ptr()), src.numel(),
+                                        _stream_handle(stream, src.device)))
+        _keep_for(stream, c)
         self.aqsntemp_c64 = c
         return self
 
@@ -113,6 +124,17 @@ def _stream_handle(stream, device):
     if stream is None:
         stream = torch.cuda.current_stream(device)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _keep_for(stream, *tensors):
+    """Tell torch's caching allocator that ``stream`` (when given) uses these tensors, which
+    were allocated on the current stream: their memory is then not handed out again until
+    the work enqueued on ``stream`` so far has finished, even once the tensors are freed."""
+    if stream is None:
+        return
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
 
 
 def make_options(precision="fp64", occ_mode="all", block_threads=0, blocks_per_sm=0,
@@ -163,6 +185,7 @@ def sigma(dp: DeviceProblem, *, out=None, workspace: torch.Tensor | None = None,
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     N.check(lib.gpp_sigma(ctypes.byref(prob), ctypes.byref(o), ctypes.c_void_p(workspace.data_ptr()),
                           workspace.numel(), _stream_handle(stream, dev)))
+    _keep_for(stream, workspace, ach, asx)
     return ach, asx
 
 
@@ -240,6 +263,7 @@ def sigma_backward(dp: DeviceProblem, grad_achtemp: torch.Tensor, grad_asxtemp: 
                                    ctypes.c_void_p(ga.data_ptr()), ctypes.c_void_p(gs.data_ptr()),
                                    ctypes.byref(grads), ctypes.c_void_p(workspace.data_ptr()),
                                    workspace.numel(), _stream_handle(stream, dev)))
+    _keep_for(stream, workspace, ga, gs, *out.values())
     return out
 
 

@@ -33,15 +33,20 @@ def restrict_columns(dp: gpp.DeviceProblem, lo: int, hi: int) -> gpp.DeviceProbl
 
 
 def reduce_outputs(ach: torch.Tensor, asx: torch.Tensor, group=None):
-    """Sum per-rank (achtemp, asxtemp) in rank order on every rank (deterministic)."""
+    """Sum per-rank (achtemp, asxtemp) in rank order on every rank (deterministic). With a
+    gloo group the 2 * nw values go through host memory (gloo's collectives are host-side);
+    the result comes back on the outputs' device."""
     world = dist.get_world_size(group)
     mine = torch.cat([torch.view_as_real(ach), torch.view_as_real(asx)]).reshape(-1)
+    dev = mine.device
+    if dist.get_backend(group) == "gloo":
+        mine = mine.cpu()
     bufs = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(bufs, mine, group=group)
     tot = bufs[0].clone()
     for b in bufs[1:]:
         tot += b
-    tot = torch.view_as_complex(tot.reshape(-1, 2))
+    tot = torch.view_as_complex(tot.reshape(-1, 2)).to(dev)
     nw = ach.numel()
     return tot[:nw].clone(), tot[nw:].clone()
 

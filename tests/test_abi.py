@@ -78,6 +78,26 @@ def test_host_side_validation(lib):
     assert lib.gpp_version().startswith(b"libgpp")
 
 
+def test_noalloc_returns_the_validation_codes(lib):
+    """gpp_sigma_noalloc reports the code gpp_sigma gives for the same bad arguments (no
+    device is touched before the arguments are validated)."""
+    from paper_2008_11326_gb300 import _native as N
+    assert lib.gpp_sigma_noalloc(None, None, None) == -1
+    assert b"problem is NULL" in lib.gpp_last_error()
+    p = N.GppProblem()
+    p.number_bands, p.nvband, p.ncouls, p.ngpown, p.nw = 4, 2, 8, 2, 0
+    assert lib.gpp_sigma_noalloc(ctypes.byref(p), None, None) == -2
+    p.nw = 3
+    o = N.GppOptions()
+    lib.gpp_options_default(ctypes.byref(o))
+    o.precision = 7
+    assert lib.gpp_sigma_noalloc(ctypes.byref(p), ctypes.byref(o), None) == -8
+    assert b"precision" in lib.gpp_last_error()
+    lib.gpp_options_default(ctypes.byref(o))
+    o.physics = 4
+    assert lib.gpp_sigma_noalloc(ctypes.byref(p), ctypes.byref(o), None) == -8
+
+
 def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     from paper_2008_11326_gb300 import _native
     monkeypatch.setattr(_native, "_lib", None)

@@ -1,7 +1,9 @@
 """The FP32-bulk kernel's branch-decision margin, checked on the CPU.
 
 The kernel decides branch 1 (|wdiff|^2 > 1/4) from d = |x - w|^2 - 1/4 evaluated in FP32
-(x and w rounded to FP32, then Ar = x - Re w, A2 = fma(Ar, Ar, (Im w)^2), d = A2 - 1/4) and
+(x and Re w each split into an FP32 value and its FP32 residual, x = x_hi + x_lo and
+Re w = wr + wr_lo; Ar = (x_hi - wr) + (x_lo - wr_lo), A2 = fma(Ar, Ar, (Im w)^2),
+d = A2 - 1/4) and
 trusts the sign of d only when |d| exceeds the margin m = 2^-20 (|x| + 252) held in its band
 table; otherwise it recomputes |wdiff|^2 in FP64. The design rests on two claims for the
 fast path (x >= 0, Re w >= 0, |w|^2 < 62499, |x| < 1e4):
@@ -28,7 +30,9 @@ MARGIN_W = F32(252.0)
 def fp32_d(x, wr, wi):
     """The kernel's FP32 d and margin for FP64 inputs."""
     x32, wr32, wi32 = x.astype(F32), wr.astype(F32), wi.astype(F32)
-    ar = (x32 - wr32).astype(F32)
+    x_lo = (x - x32.astype(np.float64)).astype(F32)
+    wr_lo = (wr - wr32.astype(np.float64)).astype(F32)
+    ar = ((x32 - wr32).astype(F32) + (x_lo - wr_lo).astype(F32)).astype(F32)
     wi2 = (wi32 * wi32).astype(F32)
     a2 = (ar.astype(np.float64) * ar.astype(np.float64) + wi2.astype(np.float64)).astype(F32)
     d = (a2 - F32(0.25)).astype(F32)

@@ -112,3 +112,41 @@ def test_rejects_mixed_nw(gpp):
     b = inputs.make_problem(3, 2, 64, 4, 2, seed=2)
     with pytest.raises(_native.GppError, match="nw"):
         gpp.BatchedPlan(device_batch(gpp, [a, b]))
+
+
+def _host_problem(d, nb):
+    """The first nb bands of a device instance, as host arrays for the oracle."""
+    return inputs.GppProblem(
+        number_bands=nb, nvband=d.nvband, ncouls=d.ncouls, ngpown=d.ngpown, nw=d.nw,
+        aqsmtemp=d.aqsmtemp[:nb].cpu().numpy(), aqsntemp=d.aqsntemp[:nb].cpu().numpy(),
+        I_eps_array=d.I_eps_array.cpu().numpy(), wtilde_array=d.wtilde_array.cpu().numpy(),
+        vcoul=d.vcoul.cpu().numpy(), inv_igp_index=d.inv_igp_index.cpu().numpy(),
+        indinv=d.indinv.cpu().numpy(), wx_array=d.wx_array[:nb].cpu().numpy())
+
+
+def test_batched_workload_against_oracle(gpp):
+    """The 64-instance batched workload (G log-uniform in [2048, 32768], P = G/20, B in
+    64..512, drawn on the device), every instance cut to its first 8 bands so that the
+    oracle takes seconds: one graph-replayed persistent launch over all 64, and four
+    instances (smallest and largest G, two in between) against the oracle, FP64 and
+    FP32-bulk."""
+    import torch
+    nb = 8
+    full = [gpp.DeviceProblem(**inputs.make_device_arrays(**s, device="cuda"))
+            for s in inputs.batched_shapes()]
+    sub = [gpp.DeviceProblem(nb, d.nvband, d.ncouls, d.ngpown, d.nw, d.aqsmtemp[:nb],
+                             d.aqsntemp[:nb], d.I_eps_array, d.wtilde_array, d.vcoul,
+                             d.inv_igp_index, d.indinv, d.wx_array[:nb]) for d in full]
+    order = sorted(range(len(sub)), key=lambda i: sub[i].ncouls)
+    picks = [order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]]
+    refs = {i: np.concatenate(oracle.sigma(_host_problem(full[i], nb))) for i in picks}
+    for precision, tol in (("fp64", 1e-12), ("fp32_bulk", 1e-6)):
+        plan = gpp.BatchedPlan(sub, use_graph=True, precision=precision)
+        outs = as_np(plan.run())
+        torch.cuda.synchronize()
+        plan.close()
+        for i in picks:
+            err = float(np.max(np.abs(outs[i] - refs[i]) / np.abs(refs[i])))
+            assert err <= tol, (precision, i, sub[i].ncouls, err)
+    del full, sub
+    torch.cuda.empty_cache()

@@ -233,3 +233,25 @@ def test_benchmark_full_size_additivity(gpp, benchmark_problem):
         acc_a += a
         acc_s += s
     assert rel_err((acc_a, acc_s), full) <= 1e-13
+
+
+def test_side_stream_call_keeps_its_memory(gpp):
+    """gpp.sigma on a stream other than the current one: the workspace and outputs it
+    allocates are recorded on that stream, so memory freed when the call returns is not
+    handed to the current stream (here a same-sized buffer filled right away) while the
+    sum still runs."""
+    import torch
+    prob = inputs.make_problem(64, 2, 8192, 96, 3, seed=19)
+    dp = gpp.DeviceProblem.from_host(prob, device="cuda")
+    ref = np.concatenate([t.cpu().numpy() for t in gpp.sigma(dp)])
+    need = gpp.workspace_size(dp)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        ach, asx = gpp.sigma(dp, stream=side)
+        junk = torch.full((need,), 0x7f, dtype=torch.uint8, device="cuda")
+        junk2 = torch.full((need,), 0x3c, dtype=torch.uint8, device="cuda")
+        side.synchronize()
+        got = np.concatenate([ach.cpu().numpy(), asx.cpu().numpy()])
+        assert np.array_equal(got, ref)
+        del junk, junk2

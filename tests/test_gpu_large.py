@@ -5,8 +5,8 @@ The full FP64 sum at this size takes over a minute, so the FP64 checks run on th
 16 bands at full P and G: the GPU result against the oracle on sampled columns (computed
 one by one on the host), and the full launch against the sum of four launches over column
 ranges (a property that holds at any size and fails on an indexing or tile-count error).
-The FP32-bulk path runs the full instance and is held to the same additivity and to the
-FP64 result on the 16-band subset.
+The FP32-bulk path runs the full instance and is held to the same additivity, and on 64
+columns with every band (the B = 1536 band loop) to the FP64 result of the same columns.
 """
 
 import numpy as np
@@ -88,8 +88,12 @@ def test_fp32_bulk_full_instance(large):
     full = np.concatenate([a.cpu().numpy(), s.cpu().numpy()])
     assert np.all(np.isfinite(full))
     assert rel(column_sum(gpp, dp, 3, precision="fp32_bulk"), full) <= 1e-6
-    sub = bands(gpp, dp, 16)
-    a32, s32 = gpp.sigma(sub, precision="fp32_bulk")
-    a64, s64 = gpp.sigma(sub)
+    # every band (the B = 1536 loop) on 64 columns, against the FP64 path on the same
+    # columns (the FP64 path matches the oracle to 1e-12)
+    cols = gpp.DeviceProblem(dp.number_bands, dp.nvband, dp.ncouls, 64, dp.nw, dp.aqsmtemp,
+                             dp.aqsntemp, dp.I_eps_array[:64], dp.wtilde_array[:64], dp.vcoul,
+                             dp.inv_igp_index[:64], dp.indinv, dp.wx_array, dp.aqsntemp_c64)
+    a32, s32 = gpp.sigma(cols, precision="fp32_bulk")
+    a64, s64 = gpp.sigma(cols)
     assert rel(np.concatenate([a32.cpu().numpy(), s32.cpu().numpy()]),
                np.concatenate([a64.cpu().numpy(), s64.cpu().numpy()])) <= 1e-6
