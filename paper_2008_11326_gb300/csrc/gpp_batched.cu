@@ -58,20 +58,50 @@ __device__ inline void bitonic_sort(float* key, int* idx, int n, int seg) {
   }
 }
 
+// The FP32-bulk kernel's general path for one (igp, ig) pair: the FP64 band loop, folded
+// into the thread's tile pairs. Not inlined: its FP64 accumulators would otherwise count
+// against the register budget of the FP32 band loop, which it shares a kernel with (and
+// the warps that take it are rare).
+template <int W>
+__device__ __noinline__ void f32_general_pair(int B, int64_t G, int nocc,
+                                              const double2* __restrict__ aqsn,
+                                              const double2* __restrict__ am,
+                                              const BandEntry* __restrict__ bt, bool live,
+                                              double wr, double wi, double Iwr, double Iwi,
+                                              double sx2, float* s_slots) {
+  double a[4 * W];
+#pragma unroll
+  for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
+  band_loop<W, false>(B, G, nocc, aqsn, am, bt, live, wr, wi, Iwr, Iwi, sx2, a);
+#pragma unroll
+  for (int qd = 0; qd < W; ++qd) {
+    float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double v = a[4 * qd + i];
+      const float h = static_cast<float>(v);
+      pair_add(quad_elem(th, i), quad_elem(tl, i), h, static_cast<float>(v - static_cast<double>(h)));
+    }
+    *F32Slots<W>::tile4(s_slots, qd) = th;
+    *F32Slots<W>::tile4(s_slots, W + qd) = tl;
+  }
+}
+
 // Tile partials: FP64 sums (double) for GPP_FP64; compensated FP32 pairs (float2, hi + lo)
 // for GPP_FP32_BULK, so that its main kernel needs no FP64 arithmetic outside the rare
-// exact-decision and near-pole branches. Both are 8 bytes per value.
-// The FP32-bulk instantiation is held to 64 registers per thread (four 256-thread CTAs per
-// SM; 80 for nw > 5, whose band loop would spill at 64): it is latency-bound, and on GB300
-// (nw = 3) it ran 253 ms at 128 registers, 178 ms at 80 and 150 ms at 64 on the benchmark
-// shape (its compensated pairs live in shared memory, and only the rare FP64 fallback path
-// spills at this budget).
+// exact-decision and near-pole branches and the once-per-pair I w. Both are 8 bytes per
+// value. The FP32-bulk instantiation is held to 72 registers per thread: with its shared
+// memory (the compensated pairs) that is 7 CTAs of 128 threads per SM either way, and on
+// GB300 (nw = 3, benchmark instance) its main kernel ran 111.2 ms at 64 registers (spilled
+// values reloaded in the band loop), 104.5 ms at 72 and 105.9 ms at 80.
+#ifndef GPP_F32_MAXNREG
+#define GPP_F32_MAXNREG 72
+#endif
 template <int W, bool F32>
-__global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_kernel(const BatchInst* __restrict__ inst,
-                                                          int ninst, int64_t t_begin,
-                                                          int64_t ntiles, int igpt,
-                                                          unsigned long long* counter,
-                                                          double* __restrict__ partials) {
+__device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst, int ninst,
+                                             int64_t t_begin, int64_t ntiles, int igpt,
+                                             unsigned long long* counter,
+                                             double* __restrict__ partials) {
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
   __shared__ const BandEntry* s_bt64;  // FP32-bulk: the FP64 band table, for the exact path
@@ -172,23 +202,8 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
       const double Iwr = fma(I.x, w.x, -I.y * w.y);
       const double Iwi = fma(I.x, w.y, I.y * w.x);
       if (F32) {  // the general path in FP64, folded into the tile pairs
-        double a[4 * W];
-#pragma unroll
-        for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
-        band_loop<W, false>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                            w.x, w.y, Iwr, Iwi, d.sx2, a);
-#pragma unroll
-        for (int qd = 0; qd < W; ++qd) {
-          float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const double v = a[4 * qd + i];
-            const float h = static_cast<float>(v);
-            pair_add(quad_elem(th, i), quad_elem(tl, i), h, static_cast<float>(v - static_cast<double>(h)));
-          }
-          *F32Slots<W>::tile4(s_slots, qd) = th;
-          *F32Slots<W>::tile4(s_slots, W + qd) = tl;
-        }
+        f32_general_pair<W>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
+                            w.x, w.y, Iwr, Iwi, d.sx2, s_slots);
       } else if (fast) {
         band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
                            w.x, w.y, Iwr, Iwi, 0.0, acc);
@@ -214,6 +229,25 @@ __global__ void __launch_bounds__(256, F32 ? (W <= 5 ? 4 : 3) : 1) gpp_batched_k
     else
       block_partials<4 * W>(acc, red, partials + t * 4 * W);
   }
+}
+
+// The two instantiations of the main kernel. FP64: one 256-thread CTA's worth of registers
+// per SM at most (the FP64 band loop takes ~160 registers). FP32-bulk: held to
+// GPP_F32_MAXNREG registers (80 for nw > 5, whose band loop would spill at fewer).
+template <int W>
+__global__ void __launch_bounds__(256, 1)
+    gpp_batched_kernel_f64(const BatchInst* __restrict__ inst, int ninst, int64_t t_begin,
+                           int64_t ntiles, int igpt, unsigned long long* counter,
+                           double* __restrict__ partials) {
+  batched_body<W, false>(inst, ninst, t_begin, ntiles, igpt, counter, partials);
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) __maxnreg__(W <= 5 ? GPP_F32_MAXNREG : 80)
+    gpp_batched_kernel_f32(const BatchInst* __restrict__ inst, int ninst, int64_t t_begin,
+                           int64_t ntiles, int igpt, unsigned long long* counter,
+                           double* __restrict__ partials) {
+  batched_body<W, true>(inst, ninst, t_begin, ntiles, igpt, counter, partials);
 }
 
 // One CTA per instance: the instance's tile partials summed in tile order, then a tree.
@@ -253,7 +287,8 @@ __global__ void __launch_bounds__(256) gpp_batched_reduce_kernel(const BatchInst
 
 template <int W, bool F32>
 const void* batched_fn() {
-  return reinterpret_cast<const void*>(&gpp_batched_kernel<W, F32>);
+  return F32 ? reinterpret_cast<const void*>(&gpp_batched_kernel_f32<W>)
+             : reinterpret_cast<const void*>(&gpp_batched_kernel_f64<W>);
 }
 
 const void* batched_kernel_ptr(int nw, bool f32) {
@@ -312,11 +347,11 @@ cudaError_t launch_batched_main(const BatchInst* inst, int ninst, int64_t ntiles
   const size_t smem = batched_smem_bytes(threads, nw, f32, igpt);
 #define GPP_BATCHED_LAUNCH(WV)                                                                    \
   if (f32)                                                                                        \
-    gpp_batched_kernel<WV, true><<<grid, threads, smem, s>>>(inst, ninst, t_begin, ntiles, igpt,  \
-                                                             counter, partials);                  \
+    gpp_batched_kernel_f32<WV><<<grid, threads, smem, s>>>(inst, ninst, t_begin, ntiles, igpt,    \
+                                                           counter, partials);                    \
   else                                                                                            \
-    gpp_batched_kernel<WV, false><<<grid, threads, 0, s>>>(inst, ninst, t_begin, ntiles, igpt,    \
-                                                           counter, partials)
+    gpp_batched_kernel_f64<WV><<<grid, threads, 0, s>>>(inst, ninst, t_begin, ntiles, igpt,       \
+                                                        counter, partials)
   switch (nw) {
     case 1: GPP_BATCHED_LAUNCH(1); break;
     case 2: GPP_BATCHED_LAUNCH(2); break;

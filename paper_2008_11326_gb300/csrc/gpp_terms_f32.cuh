@@ -108,6 +108,26 @@ __device__ __forceinline__ float& quad_elem(float4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
+// The rare exact path of a term: with `near`, the branch decided from |wdiff|^2 in FP64
+// exactly as the FP64 kernel does; with `pole` (|wdiff|^2 < 2^-30), the branch-2
+// coefficient 1/|x + w|^2 in FP64 (r, which only feeds branch 1, is then 0).
+template <int W>
+__device__ __forceinline__ void exact_decision(const BandEntry* bt64, int k, float* sp, bool near,
+                                            bool pole, bool& c1, float& b2, float& r) {
+  const double x64 = __ldg(&bt64[k].lo.x);
+  const double2 w64 = *F32Slots<W>::w64(sp);
+  const double wi2_64 = w64.y * w64.y;
+  if (near) {
+    const double a64 = x64 - w64.x;
+    c1 = gt_nonneg(fma(a64, a64, wi2_64), kLimitTwo);
+  }
+  if (pole) {
+    const double s64 = x64 + w64.x;
+    b2 = static_cast<float>(rcp_refined(fma(s64, s64, wi2_64)));
+    r = 0.0f;
+  }
+}
+
 // Bands [b0, b1) into the chunk sums c. OCC (whether these bands enter asxtemp) is a
 // template parameter: a runtime flag in this loop body costs instructions. `bt64` (the FP64
 // band table, for the rare exact path) is read from shared memory.
@@ -121,7 +141,9 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
   if (b0 >= b1) return;
   // the next band's aqsntemp and weight are loaded one band ahead (their global-memory
   // latency is the kernel's main stall); inert lanes read a valid element, and their I = 0
-  // makes every product vanish
+  // makes every product vanish. (Loading the band table's block one band ahead as well
+  // needs registers the 72-register budget does not have: the spills cost more, 124 ms
+  // against 104 ms on the benchmark instance.)
   float2 an_next = ldgf2(an_ptr + static_cast<int64_t>(b0) * G);
   float2 am_next = ldgf2(am_ptr + b0);
 #pragma unroll 1
@@ -139,8 +161,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
     const float Kwr = -Ki * q.wi, Kwi = Kr * q.wi;
     const float K2r = fmaf(Kr, q.wr, Kwr), K2i = fmaf(Ki, q.wr, Kwi);
     const float P1r = -K2i * q.w2i, P1i = K2r * q.w2i;
-    const float4* e = bt32 + static_cast<int64_t>(b) * FB;
     // the far-path block: x_hi[], the band's lowest frequency; x_lo[], its highest
+    const float4* e = bt32 + static_cast<int64_t>(b) * FB;
     float4 hq[NQ], lq[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
@@ -195,21 +217,7 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
       const bool near = fabsf(d) <= eb.z;
       const bool pole = A2 < kPoleA2;
       if (__any_sync(0xffffffffu, near || pole)) {
-        if (near || pole) {
-          const BandEntry* bt64 = *s_bt64;
-          const double x64 = __ldg(&bt64[static_cast<int64_t>(b) * W + iw].lo.x);
-          const double2 w64 = *F32Slots<W>::w64(sp);
-          const double wi2_64 = w64.y * w64.y;
-          if (near) {  // decide exactly as the FP64 kernel
-            const double a64 = x64 - w64.x;
-            c1 = gt_nonneg(fma(a64, a64, wi2_64), kLimitTwo);
-          }
-          if (pole) {  // 1/|x + w|^2 in FP64 next to the pole; r only feeds branch 1
-            const double s64 = x64 + w64.x;
-            b2 = static_cast<float>(rcp_refined(fma(s64, s64, wi2_64)));
-            r = 0.0f;
-          }
-        }
+        if (near || pole) exact_decision<W>(*s_bt64, b * W + iw, sp, near, pole, c1, b2, r);
       }
       {  // inside the interval a warp is rarely all on branch 1: no vote, select per lane
         const unsigned m = smask(c1);
@@ -313,7 +321,7 @@ __device__ __forceinline__ void two_prod(float a, float b, float& h, float& l) {
 // out as in the chunk sums: 4 iw + {Re ach, Im ach, Re asx, Im asx}, so quad iw holds the
 // two complex values of frequency iw.
 template <int W>
-__device__ __forceinline__ void fold_band_sums(float* sp, double2 Iw) {
+__device__ __noinline__ void fold_band_sums(float* sp, double2 Iw) {
   const float ar = static_cast<float>(Iw.x), ai = static_cast<float>(Iw.y);
   const float ar_l = static_cast<float>(Iw.x - static_cast<double>(ar));
   const float ai_l = static_cast<float>(Iw.y - static_cast<double>(ai));
