@@ -469,6 +469,17 @@ def run_gpu(args):
     hout = (torch.empty(prob.nw, dtype=torch.complex128).pin_memory(),
             torch.empty(prob.nw, dtype=torch.complex128).pin_memory())
     gpp.sigma_host(hp, workspace=hws, out=hout)
+    # the box's pinned host-to-device rate right now (one 268 MB copy of aqsntemp): the
+    # host entry point's copies overlap the sum, but the first chunk and aqsmtemp (which
+    # the column gather needs) are waited for
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    probe_dst = torch.empty_like(hp.aqsntemp, device=device)
+    h0.record()
+    probe_dst.copy_(hp.aqsntemp, non_blocking=True)
+    h1.record()
+    torch.cuda.synchronize(device)
+    h2d_gbs = hp.aqsntemp.numel() * 16 / (h0.elapsed_time(h1) * 1e-3) / 1e9
+    del probe_dst
     e2e_steps = max(1, args.e2e_steps)
     e2e_stage = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(e2e_steps)]
     e2e_start = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
@@ -633,6 +644,7 @@ def run_gpu(args):
                     "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": 2 * prob.nw * 16,
                     "steps": e2e_steps, "matches_device_result": e2e_ok,
                     "h2d_ms": e2e_h2d_ms, "main_kernel_ms": e2e_main_ms,
+                    "pinned_h2d_gbs": h2d_gbs,
                     "clocks": e2e_clk.summary()},
             "gpu_launches": 3 * K,
             "deterministic_across_steps": deterministic,
