@@ -578,7 +578,7 @@ def run_gpu(args):
                 "traffic": rec["traffic_bytes_per_launch"] if rec else None,
                 "algorithmic_bytes": 2.0 * prob.ngpown * prob.ncouls * 16 + prob.number_bands * prob.ncouls * 16
                 + prob.number_bands * prob.ngpown * 16 + prob.ncouls * 8 + prob.number_bands * prob.nw * 8,
-                "kernel": "gpp_batched_kernel<3, false> (main sum of gpp_sigma)",
+                "kernel": "gpp_batched_kernel_f64<3> (main sum of gpp_sigma)",
                 "peak_source": "DFMA-chain throughput kernel measured in this run, all SMs "
                                "(FP64 pipe; FMA = 2 FLOP)",
                 "achieved_source": "model FLOP (159 per band x igp x ig) / mean CUDA-event "
