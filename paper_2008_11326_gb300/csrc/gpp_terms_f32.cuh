@@ -104,6 +104,14 @@ struct F32Slots {
   }
 };
 
+// Index of value (component k, frequency iw) in the chunk sums: frequency pairs first (the
+// two frequencies of a pair adjacent, pair-aligned, for the paired FP32 instructions), then
+// the last frequency when W is odd.
+template <int W>
+__host__ __device__ constexpr int ci(int k, int iw) {
+  return iw < 2 * (W / 2) ? (k * (W / 2) + iw / 2) * 2 + (iw & 1) : 8 * (W / 2) + k;
+}
+
 __device__ __forceinline__ float& quad_elem(float4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
@@ -174,20 +182,54 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
     // branch 1 for every lane: M conj(A) / |A|^2 and M w conj(C) / |C|^2
     auto branch1 = [&](int iw, float Ar, float Sr, float S2, float r, float tr, float ti) {
       const float a1 = S2 * r;
-      c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
-      c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+      c[ci<W>(0, iw)] = fmaf(tr, a1, c[ci<W>(0, iw)]);
+      c[ci<W>(1, iw)] = fmaf(ti, a1, c[ci<W>(1, iw)]);
       if (OCC) {
         const float Yr = fmaf(Ar, Sr, q.wi2);  // Re C = Ar Sr + (Im w)^2
         const float ur = fmaf(K2r, Yr, P1r);
         const float ui = fmaf(K2i, Yr, P1i);
-        c[4 * iw + 2] = fmaf(ur, r, c[4 * iw + 2]);
-        c[4 * iw + 3] = fmaf(ui, r, c[4 * iw + 3]);
+        c[ci<W>(2, iw)] = fmaf(ur, r, c[ci<W>(2, iw)]);
+        c[ci<W>(3, iw)] = fmaf(ui, r, c[ci<W>(3, iw)]);
       }
     };
     if (xh(W) > q.hi || xl(W) < q.lo) {
       // every frequency of the band outside the warp's interval on the same side
+      // frequency pairs in GB300's paired FP32 instructions (FADD2 / FMUL2 / FFMA2: two
+      // FP32 operations per lane per instruction, each rounded as its scalar form, so the
+      // result is the scalar path's bit for bit); the chunk sums of a pair are adjacent
+      // (ci), the per-band and per-thread operands are duplicated into pairs
+      const float2 KR2 = make_float2(Kr, Kr), KI2 = make_float2(Ki, Ki);
+      const float2 KWR2 = make_float2(Kwr, Kwr), KWI2 = make_float2(Kwi, Kwi);
+      const float2 K2R2 = make_float2(K2r, K2r), K2I2 = make_float2(K2i, K2i);
+      const float2 P1R2 = make_float2(P1r, P1r), P1I2 = make_float2(P1i, P1i);
+      const float2 NWR2 = make_float2(-q.wr, -q.wr), NWRL2 = make_float2(-q.wr_lo, -q.wr_lo);
+      const float2 WR2 = make_float2(q.wr, q.wr), WI22 = make_float2(q.wi2, q.wi2);
 #pragma unroll
-      for (int iw = 0; iw < W; ++iw) {
+      for (int iw = 0; iw + 1 < W; iw += 2) {
+        const float2 XH = make_float2(xh(iw), xh(iw + 1));
+        const float2 XL = make_float2(xl(iw), xl(iw + 1));
+        const float2 AR = __fadd2_rn(__fadd2_rn(XH, NWR2), __fadd2_rn(XL, NWRL2));
+        const float2 SR = __fadd2_rn(XH, WR2);
+        const float2 A2 = __ffma2_rn(AR, AR, WI22);
+        const float2 S2 = __ffma2_rn(SR, SR, WI22);
+        const float2 DEN = __fmul2_rn(A2, S2);
+        const float2 R = make_float2(rcp_approx_f32(DEN.x), rcp_approx_f32(DEN.y));
+        const float2 A1 = __fmul2_rn(S2, R);
+        const float2 TR = __ffma2_rn(KR2, AR, KWR2);
+        const float2 TI = __ffma2_rn(KI2, AR, KWI2);
+        float2* c2 = reinterpret_cast<float2*>(c);
+        c2[ci<W>(0, iw) / 2] = __ffma2_rn(TR, A1, c2[ci<W>(0, iw) / 2]);
+        c2[ci<W>(1, iw) / 2] = __ffma2_rn(TI, A1, c2[ci<W>(1, iw) / 2]);
+        if (OCC) {
+          const float2 YR = __ffma2_rn(AR, SR, WI22);
+          const float2 UR = __ffma2_rn(K2R2, YR, P1R2);
+          const float2 UI = __ffma2_rn(K2I2, YR, P1I2);
+          c2[ci<W>(2, iw) / 2] = __ffma2_rn(UR, R, c2[ci<W>(2, iw) / 2]);
+          c2[ci<W>(3, iw) / 2] = __ffma2_rn(UI, R, c2[ci<W>(3, iw) / 2]);
+        }
+      }
+      if (W & 1) {
+        const int iw = W - 1;
         const float Ar = (xh(iw) - q.wr) + (xl(iw) - q.wr_lo);
         const float Sr = xh(iw) + q.wr;
         const float A2 = fmaf(Ar, Ar, q.wi2);
@@ -222,8 +264,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
       {  // inside the interval a warp is rarely all on branch 1: no vote, select per lane
         const unsigned m = smask(c1);
         const float a1 = msel(m, S2 * r, 0.0f);
-        c[4 * iw + 0] = fmaf(tr, a1, c[4 * iw + 0]);
-        c[4 * iw + 1] = fmaf(ti, a1, c[4 * iw + 1]);
+        c[ci<W>(0, iw)] = fmaf(tr, a1, c[ci<W>(0, iw)]);
+        c[ci<W>(1, iw)] = fmaf(ti, a1, c[ci<W>(1, iw)]);
         if (OCC) {
           // branch 2: M (-conj(S)/2) / |S|^2 = (Re M Yr - Im M Im w/2, Im M Yr + Re M Im w/2) b2
           // with Yr = -Sr/2
@@ -232,8 +274,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
           const float Yr = msel(m, fmaf(Ar, Sr, q.wi2), -0.5f * Sr);
           const float ur = fmaf(msel(m, K2r, Kr), Yr, msel(m, P1r, -Ki * wih));
           const float ui = fmaf(msel(m, K2i, Ki), Yr, msel(m, P1i, Kr * wih));
-          c[4 * iw + 2] = fmaf(ur, coef, c[4 * iw + 2]);
-          c[4 * iw + 3] = fmaf(ui, coef, c[4 * iw + 3]);
+          c[ci<W>(2, iw)] = fmaf(ur, coef, c[ci<W>(2, iw)]);
+          c[ci<W>(3, iw)] = fmaf(ui, coef, c[ci<W>(3, iw)]);
         }
       }
     }
@@ -295,7 +337,7 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
       for (int i = 0; i < 4; ++i) {
         float& hi = quad_elem(h, i);
         float& lo = quad_elem(l, i);
-        const float y = c[4 * qd + i] + lo;
+        const float y = c[ci<W>(i, qd)] + lo;
         const float t = hi + y;
         lo = y - (t - hi);
         hi = t;
