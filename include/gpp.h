@@ -175,6 +175,10 @@ GPP_API size_t gpp_sigma_host_workspace_size(const gpp_problem *prob, const gpp_
  * gpp_sigma on HOST arrays: every pointer in `prob` (inputs and outputs) is a host pointer
  * (page-locked memory gives the fastest copies and lets them overlap the sum). The inputs
  * are copied into `workspace` (a device buffer of gpp_sigma_host_workspace_size() bytes),
+ * except aqsmtemp when it is page-locked and mapped into the device's address space (as
+ * cudaHostAlloc memory is): the column gather then reads its number_bands x ngpown
+ * elements at the gathered columns in place instead of waiting for a copy of the whole
+ * array,
  * the sum runs, the outputs are copied back, and the call returns after `stream` has
  * finished (it synchronises). The copies of aqsntemp, I_eps_array and wtilde_array go in
  * up to 8 chunks of G-vectors (of doubling size, so that the sum starts after a small

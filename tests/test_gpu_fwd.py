@@ -163,11 +163,15 @@ def test_column_and_band_splits_add_up(gpp):
         assert rel_err((x[0] + y[0], x[1] + y[1]), full) <= 1e-13
 
 
-def test_host_entry_point_matches_device(gpp):
+@pytest.mark.parametrize("pin", [True, False])
+def test_host_entry_point_matches_device(gpp, pin):
+    """Page-locked host arrays (aqsmtemp's gathered columns read in place by the gather
+    kernel) and pageable ones (every input copied) give gpp_sigma's result bit for bit."""
     import torch
     prob = inputs.make_problem(6, 2, 700, 9, 3, seed=3)
     dev = run(gpp, prob)
-    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=True)
+    hp = gpp.DeviceProblem.from_host(prob, device="cpu", pin=pin)
+    assert hp.aqsmtemp.is_pinned() == pin
     ws = torch.empty(gpp.host_workspace_size(hp), dtype=torch.uint8, device="cuda")
     ach, asx = gpp.sigma_host(hp, workspace=ws)
     assert np.array_equal(ach.numpy(), dev[0]) and np.array_equal(asx.numpy(), dev[1])
