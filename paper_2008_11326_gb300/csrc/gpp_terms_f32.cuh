@@ -154,7 +154,7 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
   // against 104 ms on the benchmark instance.)
   float2 an_next = ldgf2(an_ptr + static_cast<int64_t>(b0) * G);
   float2 am_next = ldgf2(am_ptr + b0);
-#pragma unroll 2
+#pragma unroll 4
   for (int b = b0; b < b1; ++b) {
     const float2 an = an_next;
     const float2 am = am_next;
