@@ -125,7 +125,8 @@ typedef struct gpp_options {
     int32_t block_threads; /* threads per CTA of the main kernel: 0 = default (128), else a multiple of 32 in [64, 256] */
     int32_t blocks_per_sm; /* resident CTAs per SM for the persistent grid: 0 = as many as fit */
     int32_t debug_checks;  /* 1: validate indices on the device and synchronise (GPP_ERR_BAD_INDEX) */
-    int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4), max 8; a tile is
+    int32_t ig_per_thread; /* G-vectors each thread takes per tile: 0 = default (4 in GPP_FP64,
+                              2 in GPP_FP32_BULK), max 8; a tile is
                               one igp column x block_threads * ig_per_thread G-vectors x all bands */
     int32_t physics;       /* bit set of gpp_physics: 0 = the paper's sum */
     int32_t reserved;      /* must be 0 */

@@ -68,22 +68,22 @@ __device__ __noinline__ void f32_general_pair(int B, int64_t G, int nocc,
                                               const double2* __restrict__ am,
                                               const BandEntry* __restrict__ bt, bool live,
                                               double wr, double wi, double Iwr, double Iwi,
-                                              double sx2, float* s_slots) {
+                                              double sx2, float4* tp) {
   double a[4 * W];
 #pragma unroll
   for (int k = 0; k < 4 * W; ++k) a[k] = 0.0;
   band_loop<W, false>(B, G, nocc, aqsn, am, bt, live, wr, wi, Iwr, Iwi, sx2, a);
 #pragma unroll
   for (int qd = 0; qd < W; ++qd) {
-    float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
+    float4 th = tp[qd], tl = tp[W + qd];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const double v = a[4 * qd + i];
       const float h = static_cast<float>(v);
       pair_add(quad_elem(th, i), quad_elem(tl, i), h, static_cast<float>(v - static_cast<double>(h)));
     }
-    *F32Slots<W>::tile4(s_slots, qd) = th;
-    *F32Slots<W>::tile4(s_slots, W + qd) = tl;
+    tp[qd] = th;
+    tp[W + qd] = tl;
   }
 }
 
@@ -105,17 +105,22 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
   __shared__ double red[(256 / 32) * 4 * kMaxNw];
   __shared__ long long s_t;
   __shared__ const BandEntry* s_bt64;  // FP32-bulk: the FP64 band table, for the exact path
-  // FP32-bulk: the threads' slots (F32Slots: band and tile compensated pairs, FP64 wtilde;
-  // (16 W + 4) floats per thread), then the tile's G-vector positions in sorted order
+  // FP32-bulk: the threads' slots (F32Slots: band compensated pairs, FP64 wtilde; (8 W + 4)
+  // floats per thread), then the tile's G-vector positions in sorted order
   // (int[pow2_ceil(blockDim.x * igpt)]); the sort keys (float, as many) alias the start of
-  // the slots, which are written only after the sort (dynamic shared memory of
-  // batched_smem_bytes)
+  // the slots, which are written only after the sort, and the slot area is at least as long
+  // as the keys (dynamic shared memory of batched_smem_bytes)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   float* const s_slots = reinterpret_cast<float*>(dyn_smem);
   const int tile_n = blockDim.x * igpt;
   const int sort_n = F32 ? pow2_ceil(tile_n) : 0;
   float* const s_key = s_slots;
-  int* const s_pos = reinterpret_cast<int*>(s_slots + F32Slots<W>::kFloats * blockDim.x);
+  int* const s_pos = reinterpret_cast<int*>(
+      s_slots + max(F32Slots<W>::kFloats * static_cast<int>(blockDim.x), sort_n));
+  // FP32-bulk: the thread's tile sums as compensated pairs (hi quads [0, W), lo quads
+  // [W, 2W)), in local memory (the address goes to the non-inlined fold and general-path
+  // functions); touched once per (igp, ig) pair
+  float4 tpair[2 * W];
   for (;;) {
     if (threadIdx.x == 0) s_t = t_begin + static_cast<long long>(atomicAdd(counter, 1ULL));
     __syncthreads();
@@ -169,8 +174,7 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
       }
       __syncthreads();  // the keys' space becomes the threads' slots
 #pragma unroll
-      for (int k = 0; k < 2 * W; ++k)
-        *F32Slots<W>::tile4(s_slots, k) = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < 2 * W; ++k) tpair[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int j = 0; j < igpt; ++j) {
       // F32: a padding position (>= tile_n, key +inf like an inert one) can sort into the
@@ -193,8 +197,8 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
         const double2 wv = make_double2(ws[0], ws[1]);
         double2 I = make_double2(0.0, 0.0);
         if (live) I = ldg2(d.eps + p * G + ig);
-        fold_band_sums<W>(s_slots, make_double2(fma(I.x, wv.x, -I.y * wv.y),
-                                                fma(I.x, wv.y, I.y * wv.x)));
+        fold_band_sums<W>(s_slots, tpair, make_double2(fma(I.x, wv.x, -I.y * wv.y),
+                                                       fma(I.x, wv.y, I.y * wv.x)));
         continue;
       }
       double2 I = make_double2(0.0, 0.0);
@@ -203,7 +207,7 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
       const double Iwi = fma(I.x, w.y, I.y * w.x);
       if (F32) {  // the general path in FP64, folded into the tile pairs
         f32_general_pair<W>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
-                            w.x, w.y, Iwr, Iwi, d.sx2, s_slots);
+                            w.x, w.y, Iwr, Iwi, d.sx2, tpair);
       } else if (fast) {
         band_loop<W, true>(B, G, nocc, d.aqsn + (live ? ig : 0), d.am + p * B, d.bt, live,
                            w.x, w.y, Iwr, Iwi, 0.0, acc);
@@ -216,7 +220,7 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
       float hi[4 * W], lo[4 * W];
 #pragma unroll
       for (int qd = 0; qd < W; ++qd) {
-        float4 th = *F32Slots<W>::tile4(s_slots, qd), tl = *F32Slots<W>::tile4(s_slots, W + qd);
+        float4 th = tpair[qd], tl = tpair[W + qd];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           hi[4 * qd + i] = quad_elem(th, i);
@@ -308,11 +312,12 @@ const void* batched_kernel_ptr(int nw, bool f32) {
 }  // namespace
 
 size_t batched_smem_bytes(int threads, int nw, bool f32, int igpt) {
-  // F32Slots<nw>::kFloats floats per thread, then the sorted positions (the keys alias the
-  // slots: pow2_ceil(threads * igpt) <= 16 threads <= 16 nw threads floats)
-  return f32 ? static_cast<size_t>(threads) * (16 * nw + 4) * sizeof(float) +
-                   static_cast<size_t>(pow2_ceil(threads * igpt)) * sizeof(int)
-             : 0;
+  // F32Slots<nw>::kFloats floats per thread (at least as many as the sort keys, which alias
+  // them), then the sorted positions
+  if (!f32) return 0;
+  const size_t sort_n = static_cast<size_t>(pow2_ceil(threads * igpt));
+  const size_t slots = static_cast<size_t>(threads) * (8 * nw + 4);
+  return (slots > sort_n ? slots : sort_n) * sizeof(float) + sort_n * sizeof(int);
 }
 
 // A CTA whose static + dynamic shared memory exceeds 48 KB (nw >= 6 at 256 threads) must

@@ -30,7 +30,8 @@
 //    |wdiff|^2 < 2^-30 the branch-2 coefficient 1/|x + w|^2 is taken in FP64.
 //  * Accumulation. Terms are summed in FP32 over chunks of kChunk bands (the rounding error
 //    of a running FP32 sum grows with the number of terms in it), every chunk sum is added
-//    into a compensated (Kahan) FP32 pair, and once per (igp, ig) pair the pair is
+//    to a running FP32 sum with Kahan's compensation (the compensation carried into the next
+//    chunk's sum), the two forming a compensated pair, and once per (igp, ig) pair the pair is
 //    multiplied by I w in double-FP32 arithmetic (I w formed in FP64) and added into the
 //    thread's compensated tile sums; the block and final reductions are compensated pairs
 //    and FP64 (gpp_batched.cu).
@@ -84,23 +85,23 @@ struct PairF32 {
 };
 
 // The thread's slots in the FP32 path's dynamic shared memory: the band sums' compensated
-// pairs (4W hi values then 4W lo values), the tile sums' compensated pairs (likewise), each
-// stored as float4 with a stride of blockDim.x (a thread's four consecutive values in one
-// 16-byte access, conflict-free across a warp), then the thread's FP64 wtilde (double2),
-// read only on the rare exact-decision path and at the end of a pair's band loop. Kept here
-// rather than in registers, which bound the kernel's occupancy.
+// pairs (4W hi values then 4W lo values), each stored as float4 with a stride of blockDim.x
+// (a thread's four consecutive values in one 16-byte access, conflict-free across a warp),
+// then the thread's FP64 wtilde (double2), read only on the rare exact-decision path and
+// at the end of a pair's band loop. Kept here rather than in registers, which bound the
+// kernel's occupancy. (The tile sums' compensated pairs, touched once per pair, live in
+// the thread's local memory: in shared memory they would take the L1 capacity that the
+// band loop's aqsntemp loads hit in.)
 template <int W>
 struct F32Slots {
-  static constexpr int kFloats = 16 * W + 4;  // per thread
-  // band pairs: quads [0, W) hold hi[4q .. 4q + 3], quads [W, 2W) lo; tile pairs follow
+  static constexpr int kFloats = 8 * W + 4;  // per thread
+  // band pairs: quads [0, W) hold hi[4q .. 4q + 3] (the four values of frequency q: Re ach,
+  // Im ach, Re asx, Im asx), quads [W, 2W) lo
   static __device__ __forceinline__ float4* band4(float* sp, int q) {
     return reinterpret_cast<float4*>(sp) + q * blockDim.x + threadIdx.x;
   }
-  static __device__ __forceinline__ float4* tile4(float* sp, int q) {
-    return reinterpret_cast<float4*>(sp) + (2 * W + q) * blockDim.x + threadIdx.x;
-  }
   static __device__ __forceinline__ double2* w64(float* sp) {
-    return reinterpret_cast<double2*>(sp + 16 * W * blockDim.x) + threadIdx.x;
+    return reinterpret_cast<double2*>(sp + 8 * W * blockDim.x) + threadIdx.x;
   }
 };
 
@@ -301,7 +302,7 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
   q.w2i = 2.0f * q.wr * q.wi;           // Im w^2
   *F32Slots<W>::w64(sp) = w64;
 #pragma unroll
-  for (int k = 0; k < 2 * W; ++k) *F32Slots<W>::band4(sp, k) = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = 0; k < W; ++k) *F32Slots<W>::band4(sp, k) = make_float4(0.f, 0.f, 0.f, 0.f);
   {  // the warp's Re w interval (inert lanes, whose I is 0, left out)
     constexpr double kHalf = 0.5 + 9.5367431640625e-07;  // 1/2 + 2^-20
     float lo = __double2float_rd(w64.x - kHalf), hi = __double2float_ru(w64.x + kHalf);
@@ -317,35 +318,39 @@ __device__ __forceinline__ void band_loop_f32(int B, int64_t G, int nocc,
     q.lo = lo;
     q.hi = hi;
   }
+  // Kahan's summation over chunks: the running sums hi (shared memory) take each chunk sum,
+  // and the rounding error of that addition, y - (t - hi), is carried in the chunk sums c
+  // themselves (the next chunk's bands are added on top of it), so only hi is read and
+  // written per merge; the last carry becomes the pairs' lo.
+  float c[4 * W];
+#pragma unroll
+  for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
 #pragma unroll 1
   for (int b0 = 0; b0 < B; b0 += kChunk) {
-    float c[4 * W];
-#pragma unroll
-    for (int k = 0; k < 4 * W; ++k) c[k] = 0.0f;
     const int bend = min(b0 + kChunk, B);
     const int bocc = max(b0, min(nocc, bend));   // bands [b0, bocc) are occupied
     bands_f32<W, true>(b0, bocc, static_cast<int>(G), an_ptr, am_ptr, bt32, s_bt64, sp, q, c);
     if (bocc < bend)
       bands_f32<W, false>(bocc, bend, static_cast<int>(G), an_ptr, am_ptr, bt32, s_bt64, sp, q,
                           c);
-    // the chunk sums merged into the band pairs with Kahan's compensation (the pair holds
-    // the running sum as hi + lo), four values per shared-memory access
 #pragma unroll
-    for (int qd = 0; qd < W; ++qd) {
-      float4 h = *F32Slots<W>::band4(sp, qd), l = *F32Slots<W>::band4(sp, W + qd);
+    for (int qd = 0; qd < W; ++qd) {   // four values per shared-memory access
+      float4 h = *F32Slots<W>::band4(sp, qd);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float& hi = quad_elem(h, i);
-        float& lo = quad_elem(l, i);
-        const float y = c[ci<W>(i, qd)] + lo;
+        float& y = c[ci<W>(i, qd)];
         const float t = hi + y;
-        lo = y - (t - hi);
+        y = y - (t - hi);
         hi = t;
       }
       *F32Slots<W>::band4(sp, qd) = h;
-      *F32Slots<W>::band4(sp, W + qd) = l;
     }
   }
+#pragma unroll
+  for (int qd = 0; qd < W; ++qd)
+    *F32Slots<W>::band4(sp, W + qd) =
+        make_float4(c[ci<W>(0, qd)], c[ci<W>(1, qd)], c[ci<W>(2, qd)], c[ci<W>(3, qd)]);
 }
 
 // (h, l) with h + l = a b exactly for FP32 a, b (no overflow or underflow): the product
@@ -355,22 +360,22 @@ __device__ __forceinline__ void two_prod(float a, float b, float& h, float& l) {
   l = fmaf(a, b, -h);
 }
 
-// Adds I w times the thread's band sums into its tile pairs, in double-FP32 arithmetic:
+// Adds I w times the thread's band sums into its tile pairs (tp: 2W float4, hi quads then
+// lo quads, in the thread's local memory), in double-FP32 arithmetic:
 // with I w = (ar + ar_l) + i (ai + ai_l) (FP32 pairs of the FP64 product) and each band
 // sum z = zh + zl, every real product is taken as its exact FP32 product plus the
 // first-order cross terms, and added into the tile pair with pair_add. Relative error of
-// order 2^-44 per value; FP32 operations only (the FP64 pipe is narrow). Values are laid
-// out as in the chunk sums: 4 iw + {Re ach, Im ach, Re asx, Im asx}, so quad iw holds the
-// two complex values of frequency iw.
+// order 2^-44 per value; FP32 operations only (the FP64 pipe is narrow). Band and tile
+// quad iw hold the two complex values of frequency iw (Re ach, Im ach, Re asx, Im asx).
 template <int W>
-__device__ __noinline__ void fold_band_sums(float* sp, double2 Iw) {
+__device__ __noinline__ void fold_band_sums(float* sp, float4* tp, double2 Iw) {
   const float ar = static_cast<float>(Iw.x), ai = static_cast<float>(Iw.y);
   const float ar_l = static_cast<float>(Iw.x - static_cast<double>(ar));
   const float ai_l = static_cast<float>(Iw.y - static_cast<double>(ai));
 #pragma unroll
   for (int qd = 0; qd < W; ++qd) {
     float4 zh = *F32Slots<W>::band4(sp, qd), zl = *F32Slots<W>::band4(sp, W + qd);
-    float4 th = *F32Slots<W>::tile4(sp, qd), tl = *F32Slots<W>::tile4(sp, W + qd);
+    float4 th = tp[qd], tl = tp[W + qd];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {  // complex value (components 2v: re, 2v + 1: im)
       const float zrh = quad_elem(zh, 2 * v), zrl = quad_elem(zl, 2 * v);
@@ -390,8 +395,8 @@ __device__ __noinline__ void fold_band_sums(float* sp, double2 Iw) {
       pair_add(quad_elem(th, 2 * v + 1), quad_elem(tl, 2 * v + 1), p[2], e[2]);
       pair_add(quad_elem(th, 2 * v + 1), quad_elem(tl, 2 * v + 1), p[3], e[3]);
     }
-    *F32Slots<W>::tile4(sp, qd) = th;
-    *F32Slots<W>::tile4(sp, W + qd) = tl;
+    tp[qd] = th;
+    tp[W + qd] = tl;
   }
 }
 
