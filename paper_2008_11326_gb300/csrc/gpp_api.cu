@@ -150,7 +150,7 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
   if (f32) {
     pl.off_bt32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.number_bands) *
-                                  (2 * ((p.nw + 4) / 4) + p.nw) * 16);  // f32_band_quads
+                                  (2 * ((p.nw + 4) / 4)) * 16);  // f32_band_quads
     pl.off_am32 = off;
     off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * p.number_bands * 2 * sizeof(float));
     if (!p.aqsntemp_c64) {  // the library makes the complex64 copy of aqsntemp

@@ -30,14 +30,13 @@ struct alignas(32) BandEntry {
   double2 hi;  // 4x, -x/2
 };
 
-// The FP32 band table: per band, f32_band_quads(W) float4. The first 2 f32_half_quads(W)
-// hold what the far-from-threshold path reads: x_hi[0..W-1] (each frequency rounded to
-// FP32) then the minimum of the band's frequencies rounded down, padded to whole float4;
-// then x_lo[0..W-1] (the FP32 residuals x - x_hi) and the maximum rounded up, likewise (two
-// float4 for W <= 3). One float4 per frequency follows for the per-lane path: x rounded
-// down, x rounded up, the branch-decision margin (see gpp_terms_f32.cuh), 0.
+// The FP32 band table: per band, f32_band_quads(W) float4: x_hi[0..W-1] (each frequency
+// rounded to FP32) then the minimum of the band's frequencies rounded down, padded to whole
+// float4; then x_lo[0..W-1] (the FP32 residuals x - x_hi) and the maximum rounded up,
+// likewise (two float4, 32 bytes, for W <= 3). The per-lane path derives its bounds on x
+// and its decision margin from x_hi (gpp_terms_f32.cuh).
 __host__ __device__ constexpr int f32_half_quads(int W) { return (W + 4) / 4; }
-__host__ __device__ constexpr int f32_band_quads(int W) { return 2 * f32_half_quads(W) + W; }
+__host__ __device__ constexpr int f32_band_quads(int W) { return 2 * f32_half_quads(W); }
 
 // Flags written by the gather kernel: [0] some wx < 0 or NaN, [1] bad index count,
 // [2] some |wx| >= kFp32MaxX or NaN (the FP32 decision margin assumes smaller x).

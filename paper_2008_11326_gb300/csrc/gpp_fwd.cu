@@ -88,12 +88,9 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
       const float xf = static_cast<float>(x);
       const int64_t b0 = i / W, iw = i - b0 * W;
       const int nq = (W + 4) / 4;
-      float* fb = reinterpret_cast<float*>(bt32 + b0 * (2 * nq + W));
+      float* fb = reinterpret_cast<float*>(bt32 + b0 * (2 * nq));
       fb[iw] = xf;
       fb[4 * nq + iw] = static_cast<float>(x - static_cast<double>(xf));
-      bt32[b0 * (2 * nq + W) + 2 * nq + iw] =
-          make_float4(__double2float_rd(x), __double2float_ru(x),
-                      kMarginScale * (fabsf(xf) + kMarginW), 0.0f);
       if (iw == 0) {  // the band's frequency range, rounded outwards, and the padding
         float lo = __int_as_float(0x7f800000), hi = -lo;
         for (int k = 0; k < W; ++k) {

@@ -42,8 +42,9 @@
 // and a frequency x more than 1/2 + 2^-20 outside [min Re w, max Re w] is on branch 1 for
 // every lane (|wdiff| >= |x - Re w| > 1/2, and 2^-20 exceeds every FP64 rounding of
 // |wdiff|^2 near 1/4 for |x| < 1e4), whatever FP32 gives. The kernel forms that interval
-// once per (igp, ig) pair with directed rounding and tests x rounded down and up against it
-// (two comparisons, the same for the whole warp); such terms skip the decision, the
+// once per (igp, ig) pair with directed rounding and tests lower and upper bounds on x
+// against it (x_hi (1 -/+ 2^-23), formed in two FMAs; two comparisons, the same for the
+// whole warp); such terms skip the decision, the
 // margin test, the pole test and both warp votes. When every frequency of a band lies
 // beyond the interval on the same side (a per-band range, rounded outwards, against the
 // interval: one test), the band takes that path for all frequencies at once.
@@ -69,6 +70,23 @@ __device__ __forceinline__ float rcp_approx_f32(float d) {
 }
 
 __device__ __forceinline__ float2 ldgf2(const float2* p) { return __ldg(p); }
+
+// L1 eviction priorities for the band loop's read-only loads. Each band streams a new
+// aqsntemp row through L1 (a CTA's 1 KB per band, read by its four warps within a short
+// window: evict first), while every CTA on the SM walks the same small band table (80 bytes
+// per band at nw = 3: evict last), which the streaming rows would otherwise push out.
+__device__ __forceinline__ float2 ld_stream_f2(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L1::evict_first.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_keep_f4(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
 
 // Selects on the integer pipe. A plain conditional between two floats can be issued as a
 // floating-point select, which GB300 executes on its (narrow) FP64 pipe; a bitwise blend
@@ -153,14 +171,14 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
   // makes every product vanish. (Loading the band table's block one band ahead as well
   // needs registers the 72-register budget does not have: the spills cost more, 124 ms
   // against 104 ms on the benchmark instance.)
-  float2 an_next = ldgf2(an_ptr + static_cast<int64_t>(b0) * G);
+  float2 an_next = ld_stream_f2(an_ptr + static_cast<int64_t>(b0) * G);
   float2 am_next = ldgf2(am_ptr + b0);
 #pragma unroll 4
   for (int b = b0; b < b1; ++b) {
     const float2 an = an_next;
     const float2 am = am_next;
     if (b + 1 < b1) {
-      an_next = ldgf2(an_ptr + static_cast<int64_t>(b + 1) * G);
+      an_next = ld_stream_f2(an_ptr + static_cast<int64_t>(b + 1) * G);
       am_next = ldgf2(am_ptr + b + 1);
     }
     // the band sums run on M = am an; the caller multiplies them by I w (the same for
@@ -175,8 +193,8 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
     float4 hq[NQ], lq[NQ];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
-      hq[k] = __ldg(&e[k]);
-      lq[k] = __ldg(&e[NQ + k]);
+      hq[k] = ld_keep_f4(&e[k]);
+      lq[k] = ld_keep_f4(&e[NQ + k]);
     }
     auto xh = [&](int i) -> float { return quad_elem(hq[i >> 2], i & 3); };
     auto xl = [&](int i) -> float { return quad_elem(lq[i >> 2], i & 3); };
@@ -242,7 +260,12 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
     }
 #pragma unroll
     for (int iw = 0; iw < W; ++iw) {
-      const float4 eb = __ldg(&e[2 * NQ + iw]);  // x rounded down, up, margin
+      // bounds on x (x >= 0 on this path): x_hi (1 -/+ 2^-23) lie beyond the FP32
+      // neighbours of x_hi, and FLT_MIN covers an x that rounds to zero or a subnormal (the
+      // lower bound exceeds such an x only below 1/2, and it is compared only with the
+      // interval's upper end, >= 1/2 or -inf)
+      const float xrd = fmaf(xh(iw), -0x1p-23f, xh(iw));
+      const float xru = fmaf(xh(iw), 0x1p-23f, xh(iw) + 0x1p-126f);
       const float Ar = (xh(iw) - q.wr) + (xl(iw) - q.wr_lo);
       const float Sr = xh(iw) + q.wr;
       const float A2 = fmaf(Ar, Ar, q.wi2);
@@ -250,14 +273,14 @@ __device__ __forceinline__ void bands_f32(int b0, int b1, int G, const float2* _
       float r = rcp_approx_f32(A2 * S2);
       const float tr = fmaf(Kr, Ar, Kwr);
       const float ti = fmaf(Ki, Ar, Kwi);
-      if (eb.x > q.hi || eb.y < q.lo) {  // x outside the warp's interval
+      if (xrd > q.hi || xru < q.lo) {  // x outside the warp's interval
         branch1(iw, Ar, Sr, S2, r, tr, ti);
         continue;
       }
       float b2 = A2 * r;
       const float d = A2 - 0.25f;
       bool c1 = d > 0.0f;
-      const bool near = fabsf(d) <= eb.z;
+      const bool near = fabsf(d) <= kMarginScale * (fabsf(xh(iw)) + kMarginW);
       const bool pole = A2 < kPoleA2;
       if (__any_sync(0xffffffffu, near || pole)) {
         if (near || pole) exact_decision<W>(*s_bt64, b * W + iw, sp, near, pole, c1, b2, r);

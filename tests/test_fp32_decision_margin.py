@@ -4,8 +4,8 @@ The kernel decides branch 1 (|wdiff|^2 > 1/4) from d = |x - w|^2 - 1/4 evaluated
 (x and Re w each split into an FP32 value and its FP32 residual, x = x_hi + x_lo and
 Re w = wr + wr_lo; Ar = (x_hi - wr) + (x_lo - wr_lo), A2 = fma(Ar, Ar, (Im w)^2),
 d = A2 - 1/4) and
-trusts the sign of d only when |d| exceeds the margin m = 2^-20 (|x| + 252) held in its band
-table; otherwise it recomputes |wdiff|^2 in FP64. The design rests on two claims for the
+trusts the sign of d only when |d| exceeds the margin m = 2^-20 (|x| + 252) (formed in FP32
+from x_hi); otherwise it recomputes |wdiff|^2 in FP64. The design rests on two claims for the
 fast path (x >= 0, Re w >= 0, |w|^2 < 62499, |x| < 1e4):
 
   * where |d| < 0.1, the FP32 value is within m / 3 of the exact one, so a sign taken
@@ -84,3 +84,40 @@ def test_far_from_the_threshold_the_fp32_sign_is_exact():
     # and wherever the kernel trusts the FP32 sign (outside the margin) it is the exact one
     trusted = np.abs(d) > m
     assert np.all(np.sign(d[trusted]) == np.sign(de[trusted]))
+
+
+def _rn32(fr: Fraction) -> Fraction:
+    """fr rounded to the nearest FP32 value (ties to even), as an exact fraction."""
+    f = np.float32(float(fr))
+    cands = {f, np.nextafter(f, F32(np.inf)), np.nextafter(f, F32(-np.inf))}
+    best = min(cands, key=lambda c: (abs(Fraction(float(c)) - fr),
+                                     int(np.array(c, dtype=F32).view(np.uint32)) & 1))
+    return Fraction(float(best))
+
+
+def test_bounds_on_x_bracket_x():
+    """The per-lane path tests x against the warp's interval through two FMAs on x_hi = RN(x):
+    lower bound fma(x_hi, -2^-23, x_hi), upper bound fma(x_hi, 2^-23, x_hi + 2^-126), each
+    rounded once to FP32. The upper bound must be >= x everywhere on the fast path
+    (0 <= x < 1e4), including x that round to zero or to a subnormal and x next to powers
+    of two. The lower bound is compared only with the interval's upper end, max Re w + 1/2
+    rounded up (>= 1/2, since Re w >= 0 on the fast path; -inf for a warp without live
+    lanes): it must be <= x wherever it reaches 1/2, and it is <= x for every normal x."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    x = np.concatenate([
+        rng.uniform(0.0, 1e4, 3000),
+        rng.uniform(0.0, 12.0, 3000),
+        np.exp(rng.uniform(np.log(1e-46), np.log(1e-30), 1000)),
+        np.array([0.0, 1e-320, 2.0 ** -149, 2.0 ** -126, 1.0, 2.0, 4096.0, 9999.999]),
+    ])
+    p2 = 2.0 ** rng.integers(-20, 13, 1000).astype(np.float64)
+    x = np.concatenate([x, p2 * (1 + rng.uniform(-2e-7, 2e-7, 1000))])
+    x = x[(x >= 0) & (x < 1e4)]
+    step, tiny = Fraction(2) ** -23, Fraction(2) ** -126
+    for xv in x.tolist():
+        xh = Fraction(float(np.float32(xv)))
+        shifted = _rn32(xh + tiny)   # x_hi + 2^-126, rounded
+        lo = _rn32(-xh * step + xh)
+        hi = _rn32(xh * step + shifted)
+        assert Fraction(xv) <= hi, xv
+        assert lo <= Fraction(xv) or (xv < 2.0 ** -126 and lo < Fraction(1, 2)), xv
