@@ -91,6 +91,24 @@ def test_band_frequencies_on_both_sides_of_the_warp_interval(gpp):
     assert rel_err(run(gpp, prob, precision="fp64"), oracle.sigma(prob)) <= 1e-12
 
 
+def test_frequencies_at_the_edges_of_the_warp_interval(gpp):
+    """Every Re w = 1 and Im w = 0, so a warp's interval is [1/2 - 2^-20, 3/2 + 2^-20]
+    (rounded outwards). Frequencies a few 1e-7 inside either end are on branch 2, just
+    outside on branch 1: the per-lane path's bounds on x (formed from x_hi) must not call an
+    inside frequency outside, which would put it on branch 1 (a ~1e-4 error). No frequency
+    is 1 itself (the pole)."""
+    prob = inputs.make_problem(8, 2, 512, 4, 3, seed=5)
+    wt = np.full_like(prob.wtilde_array, 1.0 + 0.0j)
+    e = 2.0 ** -20
+    wx = np.array([[1.5 - 1e-7, 1.5 - 3e-7, 1.5 + e - 1e-7], [0.5 + 1e-7, 0.5 + 3e-7, 0.5 - e + 1e-7],
+                   [1.5 + e + 1e-7, 0.5 - e - 1e-7, 1.1], [1.5 + 1e-6, 0.5 - 1e-6, 2.0],
+                   [1.4999999, 1.5000001, 0.4999999], [0.5000001, 3.0, 0.0],
+                   [1.5 + e, 0.5 - e, 1.25], [1.5, 0.5, 0.75]])
+    prob = prob.replace(wtilde_array=wt, wx_array=wx)
+    assert rel_err(run(gpp, prob), oracle.sigma(prob)) <= RTOL
+    assert rel_err(run(gpp, prob, precision="fp64"), oracle.sigma(prob)) <= 1e-12
+
+
 def test_general_inputs_take_the_fp64_path(gpp):
     prob = inputs.make_problem(6, 2, 200, 6, 4, seed=77)
     wx = np.linspace(-2.5, 3.5, 24).reshape(6, 4)     # negative x
@@ -101,6 +119,25 @@ def test_general_inputs_take_the_fp64_path(gpp):
 def test_occupied_mode(gpp):
     prob = inputs.make_problem(40, 2, 600, 7, 3, seed=9)
     assert rel_err(run(gpp, prob, occ_mode="occupied"), oracle.sigma(prob, occ_mode=1)) <= RTOL
+
+
+def test_occupied_split_inside_a_chunk_sorted(gpp):
+    """Sorted passes (>= 128 bands) with the occupied bands ending inside a 16-band chunk
+    (nvband = 21): the chunk's band sums run through both instantiations of the band body,
+    and the Kahan compensation carried in the chunk sums crosses the split; ragged G."""
+    prob = inputs.make_problem(131, 21, 1000, 8, 3, seed=131)
+    for occ, mode in (("occupied", 1), ("all", 0)):
+        got = run(gpp, prob, occ_mode=occ)
+        assert rel_err(got, oracle.sigma(prob, occ_mode=mode)) <= RTOL, occ
+
+
+def test_one_frequency_deep_tiles_sorted(gpp):
+    """nw = 1, 160 threads x 8 G-vectors: the sort keys of a tile (1280 positions padded to
+    2048 floats) outnumber the threads' shared-memory slots (160 x 12 floats), so the slot
+    area is sized by the keys; the whole tile sorted (160 is not a power of two), ragged G."""
+    prob = inputs.make_problem(128, 2, 1500, 5, 1, seed=12)
+    got = run(gpp, prob, block_threads=160, ig_per_thread=8)
+    assert rel_err(got, oracle.sigma(prob)) <= RTOL
 
 
 def test_deterministic(gpp):
