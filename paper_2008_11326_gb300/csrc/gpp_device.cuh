@@ -24,10 +24,11 @@ constexpr double kFastWabs2Hi = 62499.0;
 
 constexpr int kMaxNw = 8;
 
-// One (band, iw) entry of the FP64 band table: x = wx_array[b][iw], x^2, 4x, -x/2.
+// One (band, iw) entry of the FP64 band table: x = wx_array[b][iw], x^2 and -x/2 (hi.x pads
+// the entry to 32 bytes).
 struct alignas(32) BandEntry {
   double2 lo;  // x, x^2
-  double2 hi;  // 4x, -x/2
+  double2 hi;  // 0, -x/2
 };
 
 // The FP32 band table: per band, f32_band_quads(W) float4: x_hi[0..W-1] (each frequency

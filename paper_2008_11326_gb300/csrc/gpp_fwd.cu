@@ -14,12 +14,16 @@
 // Arithmetic (paper §III v1: reciprocals instead of divides; §III v3: squared moduli).
 // With A = x - w, S = x + w, C = x^2 - w^2 = A S, K = M I w, K2 = K w:
 //   branch 1:  M sch = K / A        = K conj(A) / |A|^2
-//              M ssx = M w^2 I / C  = K2 conj(C) / |C|^2
+//              M ssx = M w^2 I / C  = K2 conj(C) / |C|^2 = (K/A - K/S) / 2
 //   branch 2:  M ssx = -M I delw / (4 delw + 2) = -(K/2) / S = -(K/2) conj(S) / |S|^2
-// (branch 2 uses delw = w / A, so 4 delw + 2 = 2 S / A). One reciprocal r = 1/(|A|^2 |S|^2)
-// serves all three denominators: 1/|A|^2 = |S|^2 r, 1/|C|^2 = r, 1/|S|^2 = |A|^2 r.
-// Branch selection picks operands (Z, Y, coefficient) for one shared complex
-// multiply-accumulate, so a warp whose lanes take different branches pays once.
+// (branch 2 uses delw = w / A, so 4 delw + 2 = 2 S / A; branch 1's partial fractions use
+// S - A = 2 w). On the fast path, where branch 3 cannot occur, asxtemp is therefore
+// (achtemp - sum K/S) / 2 over the occupied bands: two reciprocals per term, 1/|A|^2 and
+// 1/|S|^2, and no branch on the asxtemp side. The general form (both thresholds and the
+// screened-exchange cutoff) keeps one reciprocal r = 1/(|A|^2 |S|^2) for all three
+// denominators, 1/|A|^2 = |S|^2 r, 1/|C|^2 = r, 1/|S|^2 = |A|^2 r, and branch selection picks
+// operands (Z, Y, coefficient) for one shared complex multiply-accumulate, so a warp whose
+// lanes take different branches pays once.
 
 #include <cuda_runtime.h>
 
@@ -81,7 +85,7 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
   }
   for (int64_t i = tid; i < B * W; i += stride) {
     double x = wx[i];
-    bt[i] = BandEntry{make_double2(x, x * x), make_double2(4.0 * x, -0.5 * x)};
+    bt[i] = BandEntry{make_double2(x, x * x), make_double2(0.0, -0.5 * x)};
     if (!(x >= 0.0)) flags[0] = 1;
     if (!(fabs(x) < kFp32MaxX)) flags[2] = 1;
     if (bt32) {  // layout of f32_band_quads (gpp_device.cuh)
