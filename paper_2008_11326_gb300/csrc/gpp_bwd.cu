@@ -36,15 +36,16 @@ namespace {
 constexpr int kTX = 32;  // G-vectors per tile
 constexpr int kTY = 8;   // columns per tile (one column group)
 
-// One (band, iw) entry for the adjoint: x, x^2, 4x and the cotangent products that do not
-// depend on (p, ig): c_a, c_s, c_a x, 2 x^2 c_s, -c_s / 2, -x c_s / 2.
+// One (band, iw) entry for the adjoint: x, x^2 and the cotangent products that do not
+// depend on (p, ig): c_a + c_s / 2 and its product with x (the fast path's partial
+// fractions), c_a, c_s, c_a x, -c_s / 2, -x c_s / 2.
 struct alignas(32) BwdBand {
   double2 lo;     // x, x^2
-  double2 hi;     // 4x, 0
+  double2 cap;    // c_a + c_s / 2
   double2 ca;     // c_a
   double2 cs;     // c_s
   double2 cax;    // c_a x
-  double2 cs2x2;  // 2 x^2 c_s
+  double2 capx;   // (c_a + c_s / 2) x
   double2 csh;    // -c_s / 2
   double2 csxh;   // -x c_s / 2
 };
@@ -79,21 +80,63 @@ __global__ void gpp_bwd_prep_kernel(int64_t B, int W, const double* __restrict__
     const double2 cs = make_double2(gs.x, -gs.y);
     BwdBand e;
     e.lo = make_double2(x, x * x);
-    e.hi = make_double2(4.0 * x, 0.0);
+    e.cap = make_double2(ca.x + 0.5 * cs.x, ca.y + 0.5 * cs.y);
     e.ca = ca;
     e.cs = cs;
     e.cax = make_double2(ca.x * x, ca.y * x);
-    e.cs2x2 = make_double2(2.0 * x * x * cs.x, 2.0 * x * x * cs.y);
+    e.capx = make_double2(e.cap.x * x, e.cap.y * x);
     e.csh = make_double2(-0.5 * cs.x, -0.5 * cs.y);
     e.csxh = make_double2(-0.5 * x * cs.x, -0.5 * x * cs.y);
     bt[i] = e;
   }
 }
 
-// Per-term work for one band, all frequencies: accumulates GI and GW. sx2 (general form
-// only): sexcut^2 of the screened-exchange cutoff, 0 = off; where it drops ssx (x < 0 and
+// z^2 for a complex z, with the doubling of the imaginary part on the integer pipe.
+__device__ __forceinline__ double2 csq(double2 z) {
+  return make_double2(fma(z.x, z.x, -z.y * z.y), twice_alu(z.x * z.y));
+}
+
+// Per-term work for one band, all frequencies, on the fast path (every lane of the warp has
+// 1e-12 < |w|^2 < 62499 and Re w >= 0, every wx >= 0: branch 1 is exactly |x - w|^2 > 1/4,
+// branch 3 and the screened-exchange cutoff cannot occur). In partial fractions, with
+// u = 1/(x - w), v = 1/(x + w) and b1 the branch-1 predicate, the asxtemp parts are
+// w u v = (u - v)/2 and -v/2 in GI, 2 x^2 w (u v)^2 = x (u^2 - v^2)/2 and -x v^2/2 in GW, so
+//   GI = sum_iw (c_a + c_s/2) b1 u - (c_s/2) v,   GW = sum_iw (c_a + c_s/2) b1 x u^2 - (c_s/2) x v^2
+// on occupied bands (c_a b1 u and c_a b1 x u^2 on the others): two reciprocals per term and
+// a select on u only.
+template <int W, bool OCC>
+__device__ __forceinline__ void bwd_terms_fast(const BwdBand* __restrict__ e, double wr,
+                                               double wi, double wi2, double2& GI,
+                                               double2& GW) {
+#pragma unroll
+  for (int iw = 0; iw < W; ++iw) {
+    const double x = __ldg(&e[iw].lo.x);
+    const double Ar = x - wr;
+    const double A2 = fma(Ar, Ar, wi2);
+    const double ra = rcp_refined(A2);
+    const bool c1 = gt_nonneg(A2, kLimitTwo);
+    const double2 u = c1 ? make_double2(Ar * ra, wi * ra) : make_double2(0.0, 0.0);
+    const double2 uu = csq(u);
+    if (OCC) {
+      const double Sr = x + wr;
+      const double S2 = fma(Sr, Sr, wi2);        // >= |w|^2 > 1e-12
+      const double rs = rcp_refined(S2);
+      const double2 v = make_double2(Sr * rs, -wi * rs);
+      cmac(GI, __ldg(&e[iw].cap), u);
+      cmac(GI, __ldg(&e[iw].csh), v);
+      cmac(GW, __ldg(&e[iw].capx), uu);
+      cmac(GW, __ldg(&e[iw].csxh), csq(v));
+    } else {
+      cmac(GI, __ldg(&e[iw].ca), u);
+      cmac(GW, __ldg(&e[iw].cax), uu);
+    }
+  }
+}
+
+// Per-term work for one band, all frequencies, in the general form: accumulates GI and GW.
+// sx2: sexcut^2 of the screened-exchange cutoff, 0 = off; where it drops ssx (x < 0 and
 // |ssx| / |I| > sexcut, tested as in the forward) the ssx derivatives are zero.
-template <int W, bool FAST, bool OCC>
+template <int W, bool OCC>
 __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double wr,
                                           double wi, double wi2, double wabs2, double mw2r,
                                           double w2i, double2 w, double sx2, double2& GI,
@@ -104,31 +147,11 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
     const double x = lo.x, x2 = lo.y;
     const double Ar = x - wr;
     const double A2 = fma(Ar, Ar, wi2);
-    double S2, Sr = x + wr;
-    bool c1, c2;
-    if (FAST) {
-      S2 = fma(__ldg(&e[iw].hi.x), wr, A2);
-      c1 = gt_nonneg(A2, kLimitTwo);
-      c2 = true;
-    } else {
-      S2 = fma(Sr, Sr, wi2);
-      c1 = gt_nonneg(A2, kLimitTwo) && lt_nonneg(wabs2, kLimitOne * A2);
-      c2 = gt_nonneg(wabs2, kTolZero * A2);
-    }
+    const double Sr = x + wr;
+    const double S2 = fma(Sr, Sr, wi2);
+    const bool c1 = gt_nonneg(A2, kLimitTwo) && lt_nonneg(wabs2, kLimitOne * A2);
+    const bool c2 = gt_nonneg(wabs2, kTolZero * A2);
     const double r = rcp_refined(A2 * S2);
-    if (FAST && __all_sync(0xffffffffu, c1)) {
-      // every lane on branch 1: u = 1/(x - w), uv = 1/(x^2 - w^2)
-      const double2 u = make_double2(Ar * (S2 * r), wi * (S2 * r));
-      cmac(GI, __ldg(&e[iw].ca), u);
-      cmac(GW, __ldg(&e[iw].cax), cmul(u, u));
-      if (OCC) {
-        const double2 uv = make_double2((x2 + mw2r) * r, w2i * r);
-        const double2 wuv = cmul(w, uv);
-        cmac(GI, __ldg(&e[iw].cs), wuv);
-        cmac(GW, __ldg(&e[iw].cs2x2), cmul(wuv, uv));
-      }
-      continue;
-    }
     const double a1 = c1 ? S2 * r : 0.0;
     const double2 u = make_double2(Ar * a1, wi * a1);          // 1/(x - w) on branch 1
     cmac(GI, __ldg(&e[iw].ca), u);
@@ -141,12 +164,14 @@ __device__ __forceinline__ void bwd_terms(const BwdBand* __restrict__ e, double 
       const double2 h = csel(c1, wuv, v);
       const double2 T = cmul(h, csel(c1, uv, v));   // w (uv)^2 or v^2
       const double2 zero = make_double2(0.0, 0.0);
-      bool keep = true;
-      if (!FAST)
-        keep = !(sx2 > 0.0 && x < 0.0 &&
-                 (c1 ? gt_nonneg(wabs2 * wabs2 * r, sx2) : gt_nonneg(wabs2, 4.0 * sx2 * S2)));
-      const double2 ch = !keep ? zero : c1 ? __ldg(&e[iw].cs) : (c2 ? __ldg(&e[iw].csh) : zero);
-      const double2 cT = !keep ? zero : c1 ? __ldg(&e[iw].cs2x2) : (c2 ? __ldg(&e[iw].csxh) : zero);
+      const bool keep = !(sx2 > 0.0 && x < 0.0 &&
+                          (c1 ? gt_nonneg(wabs2 * wabs2 * r, sx2)
+                              : gt_nonneg(wabs2, 4.0 * sx2 * S2)));
+      const double2 cs = __ldg(&e[iw].cs);
+      const double tx2 = 2.0 * x2;
+      const double2 cs2x2 = make_double2(tx2 * cs.x, tx2 * cs.y);   // 2 x^2 c_s
+      const double2 ch = !keep ? zero : c1 ? cs : (c2 ? __ldg(&e[iw].csh) : zero);
+      const double2 cT = !keep ? zero : c1 ? cs2x2 : (c2 ? __ldg(&e[iw].csxh) : zero);
       cmac(GI, ch, h);
       cmac(GW, cT, T);
     }
@@ -231,9 +256,9 @@ __global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
       double2 GI = make_double2(0.0, 0.0), GW = make_double2(0.0, 0.0);
       const BwdBand* e = bt + static_cast<int64_t>(b) * W;
       if (fast)
-        bwd_terms<W, true, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, 0.0, GI, GW);
+        bwd_terms_fast<W, OCC>(e, wr, wi, wi2, GI, GW);
       else
-        bwd_terms<W, false, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, sx2, GI, GW);
+        bwd_terms<W, OCC>(e, wr, wi, wi2, wabs2, mw2r, w2i, w, sx2, GI, GW);
       // sum_b M w GI and sum_b M I GW: w and I are the thread's constants, applied at the end
       const double2 M = cmul(amv, an);
       cmac(gI, M, GI);

@@ -66,6 +66,20 @@ __device__ __forceinline__ double half_alu(double x) {
   return __longlong_as_double(h);
 }
 
+// 2 x on the integer pipe: one onto the exponent field. Exact for finite x below the
+// largest binade; a subnormal or zero x has its bits shifted left (also exact), a result
+// past the largest finite double becomes an infinity, infinities and NaN pass through.
+__device__ __forceinline__ double twice_alu(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long sign = b & (1LL << 63);
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  long long h = b + (1LL << 52);
+  h = (e == 0) ? (sign | ((b & ~(1LL << 63)) << 1)) : h;
+  h = (e == 0x7fe) ? (sign | 0x7ff0000000000000LL) : h;
+  h = (e == 0x7ff) ? b : h;
+  return __longlong_as_double(h);
+}
+
 // FP64 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64) refined by one
 // third-order Householder step of Newton's reciprocal iteration,
 //   e = 1 - d*y,   y' = y * (1 + e + e^2),
