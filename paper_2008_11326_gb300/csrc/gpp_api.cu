@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gpp.h"
+#include "gpp_device.cuh"
 #include "gpp_diag.h"
 #include "gpp_internal.h"
 
@@ -140,7 +141,7 @@ int make_plan(const gpp_problem& p, const gpp_options& o, gpp::FwdPlan* plan,
   }
   size_t off = 0;
   pl.off_flags = off;
-  off = gpp::align_up(off + 4 * sizeof(int));
+  off = gpp::align_up(off + gpp::kFlagBytes);
   pl.off_colvalid = off;
   off = gpp::align_up(off + static_cast<size_t>(p.ngpown) * sizeof(int));
   pl.off_bt = off;

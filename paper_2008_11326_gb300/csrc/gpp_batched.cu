@@ -143,6 +143,8 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
     const int64_t p = local - igt * d.P;
     const bool col_ok = d.colg[p] >= 0;
     const bool x_fast = d.flags[0] == 0 && (!F32 || d.flags[2] == 0);
+    // FP64: the partial fractions' bound on x / |w| (gpp_device.cuh)
+    const double wabs2_pf = F32 ? 0.0 : pf_wabs2_min(d.flags);
     double acc[4 * W];                 // FP64 sums (GPP_FP64)
 #pragma unroll
     for (int k = 0; k < 4 * W; ++k) acc[k] = 0.0;
@@ -186,7 +188,7 @@ __device__ __forceinline__ void batched_body(const BatchInst* __restrict__ inst,
       if (live) w = ldg2(d.wt + p * G + ig);
       const double wabs2 = fma(w.x, w.x, w.y * w.y);
       const bool fast_lane = w.x >= 0.0 && gt_nonneg(wabs2, kFastWabs2Lo) &&
-                             lt_nonneg(wabs2, kFastWabs2Hi);
+                             lt_nonneg(wabs2, kFastWabs2Hi) && !lt_nonneg(wabs2, wabs2_pf);
       const bool fast = __all_sync(0xffffffffu, fast_lane) && x_fast;
       if (F32 && fast) {
         band_loop_f32<W>(B, G, nocc, d.aqsn32 + (live ? ig : 0), d.am32 + p * B, d.bt32,

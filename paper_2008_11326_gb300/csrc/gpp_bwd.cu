@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
   __shared__ double2 s_a[kTY][kTX];
   __shared__ double2 s_r[kTY][kTX];
   const bool x_nonneg = flags[0] == 0;
+  const double wabs2_pf = pf_wabs2_min(flags);   // the partial fractions' bound (gpp_device.cuh)
   const int64_t ntiles = static_cast<int64_t>(ngroups) * n_ig_tiles;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
     const double w2i = 2.0 * wr * wi;
     const double2 Iw = cmul(I, w);
     const bool fast_lane = wr >= 0.0 && gt_nonneg(wabs2, kFastWabs2Lo) &&
-                           lt_nonneg(wabs2, kFastWabs2Hi);
+                           lt_nonneg(wabs2, kFastWabs2Hi) && !lt_nonneg(wabs2, wabs2_pf);
     const bool fast = __all_sync(0xffffffffu, fast_lane) && x_nonneg;
     const double2* an_ptr = aqsn + (ig < G ? ig : 0);
     const double2* am_ptr = am + (col_ok ? p : 0) * B;

@@ -40,8 +40,26 @@ __host__ __device__ constexpr int f32_half_quads(int W) { return (W + 4) / 4; }
 __host__ __device__ constexpr int f32_band_quads(int W) { return 2 * f32_half_quads(W); }
 
 // Flags written by the gather kernel: [0] some wx < 0 or NaN, [1] bad index count,
-// [2] some |wx| >= kFp32MaxX or NaN (the FP32 decision margin assumes smaller x).
+// [2] some |wx| >= kFp32MaxX or NaN (the FP32 decision margin assumes smaller x); from int
+// kFlagXmax on, the bits of max |wx| as a 64-bit integer. kFlagBytes in all.
 constexpr double kFp32MaxX = 1.0e4;
+constexpr int kFlagXmax = 4;
+constexpr size_t kFlagBytes = 4 * sizeof(int) + sizeof(unsigned long long);
+
+// The FP64 fast paths (forward and adjoint) take the asxtemp terms in partial fractions,
+// M w / (A S) = (M/A - M/S) / 2, whose subtraction loses about log2(1 + x / |w|) bits where
+// the two parts nearly cancel (x >> |w|). A warp takes them only if every lane has
+// |w| >= max|wx| / 128 (|w|^2 >= kPfRatio2 max|wx|^2), which bounds the loss to 7 bits
+// (relative errors of a few 1e-14 instead of a few 1e-16); other warps take the general
+// form, which does not cancel.
+constexpr double kPfRatio2 = 1.0 / 16384.0;
+
+// The smallest |w|^2 of a warp on the partial-fraction fast path, from the gather's flags.
+__device__ __forceinline__ double pf_wabs2_min(const int* flags) {
+  const double xmax = __longlong_as_double(
+      static_cast<long long>(*reinterpret_cast<const unsigned long long*>(flags + kFlagXmax)));
+  return kPfRatio2 * xmax * xmax;
+}
 
 // The FP32 branch-decision margin 2^-20 (|x| + kMarginW) (see gpp_terms_f32.cuh); kMarginW
 // bounds |Re w| + 2 on the fast path, where |w|^2 < kFastWabs2Hi.

@@ -88,6 +88,9 @@ __global__ void gpp_prep_kernel(int64_t B, int64_t G, int64_t P, int W,
     bt[i] = BandEntry{make_double2(x, x * x), make_double2(0.0, -0.5 * x)};
     if (!(x >= 0.0)) flags[0] = 1;
     if (!(fabs(x) < kFp32MaxX)) flags[2] = 1;
+    // max |wx|: non-negative doubles order as their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(flags + kFlagXmax),
+              static_cast<unsigned long long>(__double_as_longlong(fabs(x))));
     if (bt32) {  // layout of f32_band_quads (gpp_device.cuh)
       const float xf = static_cast<float>(x);
       const int64_t b0 = i / W, iw = i - b0 * W;
@@ -146,7 +149,7 @@ cudaError_t launch_convert_c64(const gpp_c128* src, int64_t ld_src, gpp_c64* dst
 cudaError_t launch_prep(const gpp_problem& p, const FwdPlan& plan, char* ws, bool fp32,
                         const BatchInst* desc, cudaStream_t s) {
   int* flags = reinterpret_cast<int*>(ws + plan.off_flags);
-  cudaError_t e = cudaMemsetAsync(flags, 0, 4 * sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(flags, 0, kFlagBytes, s);
   if (e != cudaSuccess) return e;
   if (fp32 && plan.convert_c64) {
     e = launch_convert_c64(p.aqsntemp, p.ncouls, reinterpret_cast<gpp_c64*>(ws + plan.off_aqsn32),

@@ -21,9 +21,10 @@ struct FwdPlan {
   int nw = 0;
   int64_t n_ig_tiles = 0; // tiles per column: ceil(G / (threads * igpt))
   int64_t ntiles = 0;     // ngpown * n_ig_tiles
-  size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count, [2] any |wx| >= 1e4
+  size_t off_flags = 0;   // int32[4]: [0] any wx < 0, [1] bad index count, [2] any |wx| >= 1e4;
+                          // then uint64: the bits of max |wx| (kFlagXmax)
   size_t off_colvalid = 0;// int32[P]: global column of each local column, or -1
-  size_t off_bt = 0;      // band table BandEntry[B][W] = {x, x^2, 4x, -x/2}
+  size_t off_bt = 0;      // band table BandEntry[B][W] = {x, x^2, 0, -x/2}
   size_t off_am = 0;      // gathered weights c128[P][B] = conj(aqsmtemp[b][g(p)]) vcoul[g(p)]
   size_t off_bt32 = 0;    // FP32-bulk only: float4[B][f32_band_quads(W)]
   size_t off_am32 = 0;    // FP32-bulk only: gathered weights c64[P][B]

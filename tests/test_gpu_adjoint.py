@@ -67,6 +67,20 @@ def test_general_path_inputs(gpp):
         assert max_rel(got[k], ref[k]) <= 1e-12, k
 
 
+@pytest.mark.parametrize("wscale", [0.1, 0.05, 0.002])
+def test_partial_fraction_bound(gpp, wscale):
+    """As the forward's test of the same name: warps whose |w| reach down to max|wx| / 128
+    take the fast path's partial fractions at their largest cancellation, smaller |w| the
+    general form; every gradient within 1e-12 of the CPU adjoint."""
+    from test_gpu_fwd import small_w_problem
+    prob = small_w_problem(wscale)
+    ga, gs = inputs.cotangents(8, 3)
+    ref = oracle.sigma_adjoint(prob, ga, gs)
+    got = gpu_grads(gpp, prob, ga, gs)
+    for k in KINDS:
+        assert max_rel(got[k], ref[k]) <= 1e-12, k
+
+
 def test_closed_forms(gpp):
     for section, x in (("adjoint", 2.0), ("adjoint_branch2", 1.25)):
         g = pins.golden()[section]

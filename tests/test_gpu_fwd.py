@@ -107,6 +107,28 @@ def test_near_threshold_fast_path(gpp):
     check(gpp, prob.replace(wx_array=wx))
 
 
+def small_w_problem(wscale, seed=41):
+    """Half of every column's G-vectors with |w| = wscale (Re w > 0, small phase), the rest
+    as drawn; the largest frequency is 12."""
+    prob = inputs.make_problem(24, 2, 512, 6, 3, seed=seed)
+    wt = prob.wtilde_array.copy()
+    ph = np.clip(np.angle(wt[:, :256]), -0.2, 0.2)
+    wt[:, :256] = wscale * np.exp(1j * ph)
+    wx = prob.wx_array.copy()
+    wx[0, 2] = 12.0
+    return prob.replace(wtilde_array=wt, wx_array=wx)
+
+
+@pytest.mark.parametrize("wscale", [0.1, 0.05, 0.002])
+def test_partial_fraction_bound(gpp, wscale):
+    """The fast path's partial fractions lose bits where x >> |w|, so a warp takes them only
+    if every |w| >= max|wx| / 128 (here 12 / 128 = 0.094): |w| = 0.1 puts warps on them at
+    their largest cancellation (x / |w| up to 120), |w| = 0.05 and 0.002 send those warps to
+    the general form (at 0.002 the partial fractions would lose ~13 bits, more than the
+    1e-12 bar allows); the other warps are ordinary. All within 1e-12 of the oracle."""
+    check(gpp, small_w_problem(wscale))
+
+
 def test_occupied_mode(gpp):
     prob = inputs.make_problem(6, 2, 300, 7, 3, seed=9)
     check(gpp, prob, occ="occupied")
