@@ -207,7 +207,7 @@ __device__ __forceinline__ void tile_reduce(double2 (*s_a)[kTX], double2 (*s_r)[
 }
 
 template <int W>
-__global__ void __launch_bounds__(kTX * kTY, 3) gpp_bwd_kernel(
+__global__ void __launch_bounds__(kTX * kTY, 2) gpp_bwd_kernel(
     int B, int64_t G, int64_t P, int nocc, int64_t group0, int ngroups, int64_t n_ig_tiles,
     const double2* __restrict__ aqsn, const double2* __restrict__ eps,
     const double2* __restrict__ wt, const double2* __restrict__ am,
