@@ -118,3 +118,20 @@ def test_a_wrong_identity_is_caught():
     wrong = 0.5 * (ach_terms + K / S).sum(axis=(0, 1, 2))
     ref = oracle.sigma(prob)[1]
     assert np.max(np.abs(wrong - ref) / np.abs(ref)) > 1e-3
+
+
+def test_cancellation_grows_with_x_over_w():
+    """Why the kernels bound the partial fractions to x / |w| <= 128: their subtraction
+    (K/A - K/S) loses about log2(x / |w|) bits of asxtemp. With every |w| = max x / R the
+    numpy form above stays within 1e-13 of the oracle at R = 128 and misses 1e-12 at
+    R = 1e6 (the kernels send such warps to the general form)."""
+    def worst(R):
+        prob = inputs.make_problem(16, 2, 64, 4, 3, seed=5)
+        wt = prob.wtilde_array
+        wt = (prob.wx_array.max() / R) * np.exp(1j * np.clip(np.angle(wt), -0.2, 0.2))
+        prob = prob.replace(wtilde_array=wt)
+        got = forward_partial_fractions(prob)[1]
+        ref = oracle.sigma(prob)[1]
+        return np.max(np.abs(got - ref) / np.abs(ref))
+    assert worst(128.0) <= 1e-13
+    assert worst(1e6) > 1e-12
